@@ -1,0 +1,346 @@
+"""Benchmark of the SparseStack sketch Y = S A on GB300 (one JSON line on rank 0).
+
+Workload (default): the single-matrix sweep configuration m = 2^22, n = 64, d = 4096, k = 8,
+A FP32 iid N(0, 1) (the incoherent family), accumulation FP16 round-to-nearest (the headline rule);
+FP32 / stochastic / dithered variants are timed beside it. A is 1 GiB, larger than the 129 MB L2,
+so no L2 flush is needed between steps. One step = one sk_apply (zero Y, one tile-kernel launch).
+
+  value      device throughput, GB/s of (A read + Y written) with A resident in HBM
+  e2e        the same metric through sk_apply_host with pinned host buffers (H2D of A and D2H of
+             Y inside the timed region)
+  roofline   the tile kernel against the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle (canonical FP16-RN sketch) on a bounded row sample, host cores
+
+--impl reference times the oracle itself (the reference arm of this comparison) on the same
+workload, each step a bounded row sample. Under torchrun (N > 1) every rank sketches its own
+matrix (independent problems, weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+WORKLOADS = {
+    # name: (m, n, d, k)
+    "sweep_m4M_n64_d4096_k8": (1 << 22, 64, 4096, 8),
+    "small_m16384_n16_d256_k4": (16384, 16, 256, 4),
+}
+DEFAULT_WORKLOAD = "sweep_m4M_n64_d4096_k8"
+METRIC = "SA sketch HBM GB/s (% of peak) FP16 vs FP32 at equal distortion; p99 solve ms"
+KERNEL_SOURCES = ["paper_2606_20195_gb300/csrc/sk_tile.cuh", "paper_2606_20195_gb300/csrc/sk_kernels.cu",
+                  "paper_2606_20195_gb300/csrc/sk_device.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(HERE, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def traffic_record(workload: str, rule: str):
+    """DRAM traffic per launch from the committed ncu summary, if it was taken on these sources."""
+    p = os.path.join(HERE, "profiles", f"tile_kernel_{workload}_{rule}_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    with open(p) as f:
+        for ln in f:
+            if "=" in ln and not ln.startswith("#"):
+                a, b = ln.split("=", 1)
+                kv[a.strip()] = b.strip()
+    if kv.get("kernel_sources_sha256_16") != kernel_hash():
+        return None
+    try:
+        return float(kv["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index: int = 0):
+        self.proc = None
+        self.path = os.path.join(HERE, "gpurun_out" if os.path.isdir(os.path.join(HERE, "gpurun_out")) else ".",
+                                 f".clocks_{os.getpid()}.csv")
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for ln in f:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sms.append(float(parts[1]))
+                    maxs.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(m_total: int, n: int, d: int, k: int, budget_s: float, seed: int = 0):
+    """Oracle canonical FP16-RN sketch on a row sample; returns (GB/s, cores, sample description)."""
+    import oracle
+    from paper_2606_20195_gb300 import inputs
+    rows = min(m_total, 1 << 20)
+    A = inputs.host_matrix(rows, n, "incoherent", seed=seed)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.sketch_canonical(A, d, k, seed, oracle.FP16_RN, max(1, rows // 32))
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s or reps >= 20:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    gbps = (rows * n * 4 + d * n * 2) / dt / 1e9
+    sample = f"{rows} of {m_total} rows (n={n}, d={d}, k={k}), canonical FP16-RN, {reps} reps"
+    return gbps, oracle.num_threads(), sample
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    m, n, d, k = WORKLOADS[args.workload]
+    import oracle
+    from paper_2606_20195_gb300 import inputs
+    rows = min(m, 1 << 20)
+    A = inputs.host_matrix(rows, n, "incoherent", seed=0)
+    R = max(1, rows // 32)
+    for _ in range(args.warmup):
+        oracle.sketch_canonical(A, d, k, 0, oracle.FP16_RN, R)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sketch_canonical(A, d, k, 0, oracle.FP16_RN, R)
+    dt = (time.perf_counter() - t0) / args.steps
+    gbps = (rows * n * 4 + d * n * 2) / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbps, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f16", "data": "synthetic",
+        "config": {"workload": args.workload, "m": m, "n": n, "d": d, "k": k, "rule": "fp16_rn",
+                   "sample_rows": rows},
+        "cpu_baseline": {"value": gbps, "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{rows} of {m} rows per step, canonical FP16-RN"},
+        "e2e": {"value": gbps, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--rule", default="fp16_rn", choices=["fp32", "fp16_rn", "fp16_sr", "fp16_dither"])
+    ap.add_argument("--no-extras", action="store_true", help="skip variants, distortion, cpu baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2606_20195_gb300 import _build, inputs, sk
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    sk.load()
+
+    m, n, d, k = WORKLOADS[args.workload]
+    rule = sk.RULES[args.rule]
+    # Host matrix (pinned) for e2e; a device copy for the resident measurement. Each rank gets its
+    # own independent matrix (seed = rank).
+    A_h = inputs.host_matrix(m, n, "incoherent", seed=rank)
+    A_pin = torch.from_numpy(A_h).pin_memory()
+    A = A_pin.to(dev)
+    Yb = torch.empty((d, n), dtype=torch.float32 if rule == 0 else torch.float16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(plan_h, rule_v, steps, warmup):
+        Y = torch.empty((d, n), dtype=torch.float32 if rule_v == 0 else torch.float16, device=dev)
+        for _ in range(warmup):
+            sk.sk_apply(plan_h, A, n, n, Y, stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for s in range(steps):
+            sk.sk_apply(plan_h, A, n, n, Y, stream)
+            evs[s + 1].record(stream)
+        torch.cuda.synchronize()
+        per = [evs[s].elapsed_time(evs[s + 1]) for s in range(steps)]
+        total = evs[0].elapsed_time(evs[-1])
+        return total, per, Y
+
+    plan = sk.Plan(d, m, k, rule, seed=1234 + rank)
+    with ClockSampler(local) as clk:
+        total_ms, per_ms, Y = timed(plan.handle, rule, args.steps, args.warmup)
+    clocks = clk.summary()
+    launches_per_step = plan.get(sk.SK_PARAM_LAST_LAUNCHES)
+    R_used = plan.get(sk.SK_PARAM_LAST_CHUNK_ROWS)
+    t = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    es = 4 if rule == 0 else 2
+    bytes_step = m * n * 4 + d * n * es
+    value = world * bytes_step * args.steps / (max_ms * 1e-3) / 1e9
+
+    # e2e through the host-buffer entry point (pinned A in, pinned Y out)
+    Y_pin = torch.empty((d, n), dtype=torch.float32 if rule == 0 else torch.float16).pin_memory()
+    for _ in range(2):
+        sk.sk_apply_host(plan.handle, A_pin.data_ptr(), n, n, Y_pin.data_ptr(), stream)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sk.sk_apply_host(plan.handle, A_pin.data_ptr(), n, n, Y_pin.data_ptr(), stream)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_launches = plan.get(sk.SK_PARAM_LAST_LAUNCHES)
+    te = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * bytes_step / float(te.item()) / 1e9
+
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_note = "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if peak else "fallback 6800 GB/s"
+    peak = peak or 6800.0
+    avg_launch_ms = statistics.mean(per_ms)
+    achieved = bytes_step / (avg_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_record(args.workload, args.rule), "peak_source": peak_note,
+                "kernel": f"sk::tile_kernel<{args.rule}>",
+                "algorithmic_bytes_per_launch": bytes_step}
+
+    extras = {}
+    cpu_baseline = None
+    if rank == 0 and not args.no_extras:
+        # Variants at the same workload (a few steps each).
+        variants = {}
+        etas = {}
+        for name, rv in sk.RULES.items():
+            p2 = sk.Plan(d, m, k, rv, seed=1234)
+            tot, per, Yv = timed(p2.handle, rv, 5, 3)
+            es2 = 4 if rv == 0 else 2
+            variants[name] = {"GB/s": (m * n * 4 + d * n * es2) / (statistics.mean(per) * 1e-3) / 1e9,
+                              "ms": statistics.mean(per)}
+            if name in ("fp32", "fp16_rn"):
+                etas[name] = Yv.double().cpu().numpy()
+            p2.close()
+        # Distortion eta(S, Q) of the column space of A (A = Q R_A), FP16 vs FP32 (same S).
+        import oracle
+        R_A = oracle.tall_r_factor(A_h)
+        eta = {nm: oracle.distortion_of(Yv, R_A) for nm, Yv in etas.items()}
+        extras["variants"] = variants
+        extras["distortion"] = {"eta_fp32": eta["fp32"], "eta_fp16_rn": eta["fp16_rn"],
+                                "rel_diff": abs(eta["fp16_rn"] - eta["fp32"]) / eta["fp32"],
+                                "gaussian_reference_sqrt_n_over_d": float(np.sqrt(n / d))}
+        extras["fp16_vs_fp32_speedup"] = variants["fp16_rn"]["GB/s"] / variants["fp32"]["GB/s"]
+        gb, cores, sample = cpu_oracle_rate(m, n, d, k, budget_s=10.0)
+        cpu_baseline = {"value": gb, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f16" if rule != 0 else "f32",
+            "data": "synthetic (seeded iid N(0,1) matrix per rank; paper publishes no number for this workload)",
+            "config": {"workload": args.workload, "m": m, "n": n, "d": d, "k": k, "rule": args.rule,
+                       "chunk_rows": R_used, "l2": "inputs larger than L2 (1 GiB A), no flush",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "roofline": roofline,
+            "cpu_baseline": cpu_baseline,
+            "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": m * n * 4,
+                    "d2h_bytes_per_step": d * n * es, "launches_per_step": e2e_launches},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            **extras,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * sk.h — C ABI of the GB300 SparseStack sketching library (libsk.so).
+ *
+ * The library forms Y = S*A for a tall FP32 matrix A (m x n, m >> n) with a SparseStack sparse
+ * oblivious subspace embedding S (d x m): every column of S holds exactly k nonzeros of value
+ * +-1/sqrt(k), one in each block of B = d/k consecutive rows; k = 1 is CountSketch
+ * (paper Sec. 2.2, Definition of SparseStack; Sec. 4.1 for the block ranges and the scaling).
+ * The sum is accumulated in FP32, or stored in binary16 under deterministic round-to-nearest,
+ * exact stochastic or dithered rounding (paper Sec. 4.2). S is never stored: the kernels
+ * regenerate it from a counter-based hash of (seed, row, block).
+ *
+ * Conventions for every entry point
+ *   - Pointers named *_dev are CUDA device pointers; *_host are host pointers. The caller owns
+ *     every buffer it passes; the library never frees them. A plan owns only its own scratch.
+ *   - A is row-major with row stride lda >= n elements (A[i*lda + c]); Y is row-major d x n with
+ *     row stride n; b is a vector of m floats; x is a vector of n floats.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Device work is
+ *     enqueued on it; calls return once the work is enqueued, except where stated.
+ *   - Arguments are validated before any work is enqueued; an invalid call enqueues nothing and
+ *     returns SK_ERR_INVALID_ARG (or SK_ERR_UNSUPPORTED for valid but unsupported sizes).
+ *     sk_last_error() then holds a message for the calling thread. Asynchronous device faults
+ *     surface as SK_ERR_CUDA on a later call. Nothing aborts the process.
+ *   - A plan may be used from one host thread at a time; distinct plans are independent.
+ */
+#ifndef SK_H_
+#define SK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SK_API __attribute__((visibility("default")))
+#else
+#define SK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SK_OK = 0,
+  SK_ERR_INVALID_ARG = 1, /* bad sizes, null or misaligned pointers, unknown keys */
+  SK_ERR_UNSUPPORTED = 2, /* valid request outside what this build implements (limits below) */
+  SK_ERR_OOM = 3,         /* device or host allocation failed */
+  SK_ERR_CUDA = 4,        /* a CUDA runtime call failed (message in sk_last_error) */
+  SK_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  SK_ERR_NUMERIC = 6      /* a non-finite or singular value where a finite one is required */
+} sk_status;
+
+/* Accumulation / storage rule of Y (paper Sec. 4.2). */
+typedef enum {
+  SK_FP32 = 0,       /* Y is float; contributions added in FP32 */
+  SK_FP16_RN = 1,    /* Y is binary16; each contribution rounded to nearest even */
+  SK_FP16_SR = 2,    /* Y is binary16; exact stochastic rounding of each contribution */
+  SK_FP16_DITHER = 3 /* Y is binary16; uniform dither of ~1 binary16 ulp, then nearest even */
+} sk_rule;
+
+/* Plan parameters for sk_plan_set / sk_plan_get. */
+typedef enum {
+  /* R, the chunk length in rows (>= 1). Contributions of the rows of one chunk that reach the same
+   * output are summed in FP32 before the chunk total is scaled, rounded (FP16 rules) and added into
+   * Y; chunk t holds the rows floor(i/R) == t. R = 1 is the paper's per-element scheme. 0 (the
+   * default) lets the library pick R from the tuning table for (m, n, d, k). */
+  SK_PARAM_CHUNK_ROWS = 1,
+  /* Execution order. SK_MODE_ATOMIC (default): chunk totals are added into Y in whatever order the
+   * GPU finishes them, and rows inside a chunk in any order. SK_MODE_DETERMINISTIC: the canonical
+   * order (rows ascending inside a chunk, chunks ascending), bit for bit; slow, for verification.
+   * SK_MODE_SERIAL_TILE: the fast tile kernel run by one warp of one CTA, which also follows the
+   * canonical order; for verifying the fast kernel's arithmetic (slow). */
+  SK_PARAM_MODE = 2,
+  /* Global index of the first row of A passed to sk_apply (for row-sharded matrices: S and the
+   * chunk index depend on the global row). Default 0. */
+  SK_PARAM_ROW_OFFSET = 3,
+  /* Kernel choice: SK_KERNEL_AUTO (default), SK_KERNEL_TILE (on-chip chunk accumulation),
+   * SK_KERNEL_LITERAL (one global atomic per element and nonzero, the paper's design; R must be 1). */
+  SK_PARAM_KERNEL = 4,
+  /* Columns per work item of the tile kernel (4, 8, 16 or 32; 0 = automatic). */
+  SK_PARAM_TILE_COLS = 5,
+  /* Threads per CTA of the tile kernel (128..1024, multiple of 32; 0 = automatic). */
+  SK_PARAM_THREADS = 6,
+  /* Read-only: number of kernel launches the last sk_apply/sk_solve enqueued. */
+  SK_PARAM_LAST_LAUNCHES = 7,
+  /* Read-only: the chunk length R the last sk_apply used. */
+  SK_PARAM_LAST_CHUNK_ROWS = 8
+} sk_param;
+
+enum { SK_MODE_ATOMIC = 0, SK_MODE_DETERMINISTIC = 1, SK_MODE_SERIAL_TILE = 2 };
+enum { SK_KERNEL_AUTO = 0, SK_KERNEL_TILE = 1, SK_KERNEL_LITERAL = 2 };
+
+typedef struct sk_plan_s* sk_plan;
+
+/* Library version as major*10000 + minor*100 + patch. */
+SK_API int32_t sk_version(void);
+
+/* Message describing the last failed call on this host thread ("" if none). */
+SK_API const char* sk_last_error(void);
+
+/*
+ * sk_plan_create — a sketch plan for S (d x m) with k nonzeros per column, rounding rule `rule`
+ * and sketch seed `seed` (paper Sec. 2.2 Definition of SparseStack, Sec. 4.1).
+ *   d    rows of S, d >= 1, d % k == 0 (the paper assumes divisibility; others are rejected)
+ *   m    columns of S = rows of A (>= 1); m * ceil(k/2) must stay below 2^62
+ *   k    nonzeros per column, 1 <= k <= 64 (k = 1: CountSketch)
+ *   rule one of sk_rule
+ *   seed 64-bit seed; S and the rounding random bits are pure functions of it
+ *   out  receives the plan (set to NULL on failure)
+ * Host only: enqueues no device work and allocates no device memory.
+ */
+SK_API sk_status sk_plan_create(int64_t d, int64_t m, int32_t k, int32_t rule, uint64_t seed, sk_plan* out);
+
+/* Set / read a plan parameter (sk_param). Unknown keys or out-of-range values: SK_ERR_INVALID_ARG. */
+SK_API sk_status sk_plan_set(sk_plan plan, int32_t key, int64_t value);
+SK_API sk_status sk_plan_get(sk_plan plan, int32_t key, int64_t* value);
+
+/*
+ * sk_apply — Y_dev = S * A_dev (paper Sec. 4.1 scatter, Sec. 4.2 FP16 variants).
+ *   A_dev  device, m x n FP32 rows with stride lda (>= n); 16-byte alignment of A_dev and
+ *          lda % 4 == 0 enable vector loads (other layouts are accepted and run slower)
+ *   n      columns, 1 <= n <= 65535
+ *   Y_dev  device, d x n, float (SK_FP32) or binary16 (FP16 rules), 4-byte aligned. Overwritten:
+ *          the call zeroes Y on `stream` before accumulating.
+ * The rows processed are the plan's m rows starting at global row SK_PARAM_ROW_OFFSET.
+ */
+SK_API sk_status sk_apply(sk_plan plan, const float* A_dev, int64_t lda, int64_t n, void* Y_dev, void* stream);
+
+/*
+ * sk_apply_host — the same result from HOST buffers: A_host is copied to the device in row tiles
+ * (pinned memory gives overlapped asynchronous copies; pageable memory is accepted), the tiles are
+ * sketched as they arrive, and Y is copied back to Y_host. Blocks until Y_host is written.
+ * Device staging buffers are allocated on first use and kept by the plan.
+ */
+SK_API sk_status sk_apply_host(sk_plan plan, const float* A_host, int64_t lda, int64_t n, void* Y_host, void* stream);
+
+/*
+ * sk_solve — sketch-and-solve least squares (paper Sec. 5.1): x = argmin ||(S A) x - (S b)||_2.
+ * SA and Sb are formed with this plan's S and rule (Sb uses the same chunking, as column n of
+ * [A | b]), converted to FP64, factored by a Householder QR on the device, and x is recovered by
+ * Q^T (S b) and back substitution, all in FP64; x is written as FP32.
+ *   A_dev, lda, n as in sk_apply; requires n <= d and n <= 512.
+ *   b_dev  device, m floats; x_dev device, n floats.
+ * Device scratch (d x (n+1) sketch and FP64 workspace) is allocated on first use and grown as
+ * needed; calls after the first with the same or smaller n allocate nothing.
+ * A rank-deficient SA (a zero pivot in the QR) is reported by sk_solve_status.
+ */
+SK_API sk_status sk_solve(sk_plan plan, const float* A_dev, int64_t lda, int64_t n, const float* b_dev, float* x_dev,
+                   void* stream);
+
+/* Status of the last sk_solve on this plan: synchronizes `stream`, then reads the device status
+ * word. SK_ERR_NUMERIC: SA was rank deficient (zero pivot; x was set to NaN). SK_ERR_TIMEOUT: a
+ * grid barrier of the QR kernel gave up waiting. Also writes the FP64 estimate
+ * kappa(SA) ~ max|R_ii| / min|R_ii| (>= 1) if kappa != NULL. */
+SK_API sk_status sk_solve_status(sk_plan plan, double* kappa, void* stream);
+
+/*
+ * sk_materialize_S — write the nonzero pattern of S for rows [i0, i0+cnt) on the device:
+ * rows_dev[(i-i0)*k + j] = target row of block j (int32), signs_dev[...] = +1 or -1 (int8).
+ * The same generator the sketch kernels use; for verification of the pattern.
+ */
+SK_API sk_status sk_materialize_S(sk_plan plan, int64_t i0, int64_t cnt, int32_t* rows_dev, int8_t* signs_dev,
+                           void* stream);
+
+/*
+ * Batched uneven sketches in one persistent launch (row tiles of every matrix drawn from one
+ * device work list). item i sketches A_i (m_i x n_i, stride lda_i) into Y_i (d_i x n_i) with
+ * k_i nonzeros per column, seed_i, and the batch's common rule. Items are independent.
+ * The work list is built on the host and copied to the device inside the call; a batch object
+ * keeps it so the launch can be replayed (and captured in a CUDA graph) with sk_batch_launch.
+ */
+typedef struct {
+  const float* A_dev;
+  void* Y_dev;
+  int64_t m, n, lda, d;
+  int32_t k;
+  int32_t pad_;
+  uint64_t seed;
+} sk_batch_item;
+
+typedef struct sk_batch_s* sk_batch;
+
+/* Build a batch: validates every item, chooses tiles (threads, columns per work item, chunk rows)
+ * from the tuning table unless overridden by sk_batch_set, and uploads the work list.
+ * Allocates device memory for the work list (kept by the batch). */
+SK_API sk_status sk_batch_create(const sk_batch_item* items, int32_t count, int32_t rule, sk_batch* out);
+/* Override the tile choice: key is SK_PARAM_TILE_COLS, SK_PARAM_THREADS or SK_PARAM_CHUNK_ROWS;
+ * must be called before the first sk_batch_launch. */
+SK_API sk_status sk_batch_set(sk_batch batch, int32_t key, int64_t value);
+/* Zero every Y_i and run the persistent kernel on `stream`: no allocation, no host sync, so the
+ * call can be captured into a CUDA graph and replayed. */
+SK_API sk_status sk_batch_launch(sk_batch batch, void* stream);
+/* Work-list statistics: number of work items and total bytes of A the batch reads. */
+SK_API sk_status sk_batch_info(sk_batch batch, int64_t* work_items, int64_t* bytes_A);
+SK_API void sk_batch_destroy(sk_batch batch);
+
+/* Release the plan and its device scratch (synchronizes the device first). NULL is a no-op. */
+SK_API void sk_destroy(sk_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SK_H_ */

@@ -1,0 +1,593 @@
+// C ABI of libsk: plan objects, argument validation, kernel dispatch, the host-buffer pipeline
+// and the sketch-and-solve driver. Declarations and contracts: include/sk.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/sk.h"
+#include "sk_hostutil.h"
+#include "sk_internal.h"
+#include "sk_tile.cuh"
+
+namespace sk {
+
+namespace {
+thread_local char g_err[512] = {0};
+}
+
+sk_status set_error(sk_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+const char* last_error_message() { return g_err; }
+
+}  // namespace sk
+
+using namespace sk;
+
+struct sk_plan_s {
+  int64_t d = 0, m = 0, B = 0;
+  int32_t k = 0, rule = 0;
+  uint64_t seed = 0;
+  float scale = 1.f;
+  // parameters
+  int64_t R = 0;
+  int32_t mode = SK_MODE_ATOMIC;
+  int64_t row_offset = 0;
+  int32_t kernel = SK_KERNEL_AUTO;
+  int32_t tile_cols = 0;
+  int32_t threads = 0;
+  int64_t last_launches = 0, last_R = 0;
+  // device scratch
+  float* det_P = nullptr;
+  size_t det_P_bytes = 0;
+  void* solve_buf = nullptr;
+  size_t solve_bytes = 0;
+  size_t solve_status_off = 0, solve_kappa_off = 0;
+  // host-pipeline staging
+  float* stage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  void* ydev = nullptr;
+  size_t ydev_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_used[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+constexpr int32_t kMaxK = 64;
+constexpr int64_t kMaxN = 65535;
+constexpr int32_t kMaxSolveN = 512;
+
+sk_status cuda_fail(cudaError_t e, const char* what) {
+  return set_error(SK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DevInfo {
+  int sms = 0, optin = 0;
+};
+
+sk_status dev_info(DevInfo* di) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  cudaDeviceGetAttribute(&di->sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&di->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return SK_OK;
+}
+
+size_t elem_size(int32_t rule) { return rule == SK_FP32 ? 4 : 2; }
+
+// Tile-kernel configuration for a plan and a column count.
+struct TileCfg {
+  int32_t NC = 0, kb = 0, threads = 0, grid = 0;
+  int64_t R = 0;
+  bool serial = false;
+};
+
+sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, TileCfg* cfg) {
+  const bool serial = (p->mode == SK_MODE_SERIAL_TILE);
+  const int32_t threads = serial ? 32 : (p->threads > 0 ? p->threads : 1024);
+  const size_t hbytes = (size_t)(threads / 32) * 32 * 8;
+  const size_t optin = (size_t)std::min(di.optin, 232448);
+  if (optin <= hbytes + 1024) return set_error(SK_ERR_UNSUPPORTED, "shared memory too small");
+  const size_t budget_floats = (optin - hbytes - 1024) / 4;
+  const int32_t widths[4] = {32, 16, 8, 4};
+  int32_t NC = 0, kb = 0;
+  for (int32_t c : widths) {
+    if (p->tile_cols > 0 && c != p->tile_cols) continue;
+    if (!serial && c > 4 && c / 2 >= n) continue;
+    // Serial (verification) mode needs the lane groups of a pass to hit distinct blocks.
+    if (serial && (32 / c > p->k || p->k % (32 / c) != 0)) continue;
+    if ((size_t)tile_acc_floats((uint32_t)p->B, p->k, tile_slots(c, p->k), c) <= budget_floats) {
+      NC = c;
+      kb = p->k;
+      break;
+    }
+  }
+  if (NC == 0 && !serial) {
+    NC = p->tile_cols > 0 ? p->tile_cols : 4;
+    for (int32_t kbt = p->k; kbt >= 1; --kbt) {
+      if ((size_t)tile_acc_floats((uint32_t)p->B, kbt, tile_slots(NC, kbt), NC) <= budget_floats) {
+        kb = kbt;
+        break;
+      }
+    }
+  }
+  if (NC == 0 || kb == 0)
+    return set_error(SK_ERR_UNSUPPORTED,
+                     "tile kernel: a block of %lld rows does not fit in shared memory with the requested width",
+                     (long long)p->B);
+  const int64_t ncg = (n + NC - 1) / NC;
+  const int64_t nbg = (p->k + kb - 1) / kb;
+  int64_t R = p->R;
+  if (R <= 0) {
+    // One wave of work items over the SMs, at most 32 chunks per output (each output then receives
+    // at most 32 rounded contributions), chunk rows a multiple of 32.
+    const int64_t slots = (int64_t)di.sms;
+    int64_t chunks = (slots + ncg * nbg - 1) / (ncg * nbg);
+    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, 32));
+    R = (rows + chunks - 1) / chunks;
+    R = std::max<int64_t>(32, ((R + 31) / 32) * 32);
+  }
+  cfg->NC = NC;
+  cfg->kb = kb;
+  cfg->threads = threads;
+  cfg->grid = serial ? 1 : 0;
+  cfg->R = R;
+  cfg->serial = serial;
+  return SK_OK;
+}
+
+sk_status validate_apply(const sk_plan_s* p, const void* A, int64_t lda, int64_t n, const void* Y) {
+  if (!p) return set_error(SK_ERR_INVALID_ARG, "plan is NULL");
+  if (!A) return set_error(SK_ERR_INVALID_ARG, "A is NULL");
+  if (!Y) return set_error(SK_ERR_INVALID_ARG, "Y is NULL");
+  if (n < 1 || n > kMaxN) return set_error(SK_ERR_INVALID_ARG, "n=%lld outside [1, %lld]", (long long)n, (long long)kMaxN);
+  if (lda < n) return set_error(SK_ERR_INVALID_ARG, "lda=%lld < n=%lld", (long long)lda, (long long)n);
+  if ((reinterpret_cast<uintptr_t>(A) & 3u) != 0) return set_error(SK_ERR_INVALID_ARG, "A must be 4-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(Y) & 3u) != 0) return set_error(SK_ERR_INVALID_ARG, "Y must be 4-byte aligned");
+  if (p->m > (int64_t)1 << 40 || lda > ((int64_t)1 << 40) / std::max<int64_t>(p->m, 1))
+    return set_error(SK_ERR_UNSUPPORTED, "A larger than 2^40 elements");
+  return SK_OK;
+}
+
+// Enqueue Y = S * A for rows [row_begin, row_begin + rows) (A row 0 = row_begin) with chunk rows R.
+// Y must already be zero.
+sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, int64_t row_begin, int64_t rows, void* Y,
+                         int64_t R_fixed, cudaStream_t st, int32_t* launches, int64_t* R_used) {
+  DevInfo di;
+  sk_status s = dev_info(&di);
+  if (s != SK_OK) return s;
+  const int64_t row_end = row_begin + rows;
+  const bool literal = (p->kernel == SK_KERNEL_LITERAL);
+  if (p->mode == SK_MODE_DETERMINISTIC) {
+    int64_t R = R_fixed > 0 ? R_fixed : p->R;
+    if (R <= 0) {
+      TileCfg cfg;
+      s = choose_tile(p, n, p->m, di, &cfg);
+      if (s != SK_OK) return s;
+      R = literal ? 1 : cfg.R;
+    }
+    const size_t need = sizeof(float) * (size_t)(p->d * n);
+    if (p->det_P_bytes < need) {
+      if (p->det_P) cudaFree(p->det_P);
+      p->det_P = nullptr;
+      p->det_P_bytes = 0;
+      if (cudaMalloc(&p->det_P, need) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SK_ERR_OOM, "deterministic-mode scratch (%zu bytes)", need);
+      }
+      p->det_P_bytes = need;
+    }
+    DetLaunch L;
+    L.A = A;
+    L.Y = Y;
+    L.P = p->det_P;
+    L.lda = lda;
+    L.n = n;
+    L.row_begin = row_begin;
+    L.row_end = row_end;
+    L.d = p->d;
+    L.k = p->k;
+    L.rule = p->rule;
+    L.seed = p->seed;
+    L.scale = p->scale;
+    L.R = R;
+    cudaError_t e = launch_det(L, st, launches);
+    if (e != cudaSuccess) return cuda_fail(e, "deterministic kernel launch");
+    if (R_used) *R_used = R;
+    return SK_OK;
+  }
+  if (literal) {
+    if (p->R > 1 || R_fixed > 1) return set_error(SK_ERR_INVALID_ARG, "the literal kernel implements chunk rows R = 1 only");
+    LiteralLaunch L;
+    L.A = A;
+    L.Y = Y;
+    L.lda = lda;
+    L.n = n;
+    L.row_begin = row_begin;
+    L.row_end = row_end;
+    L.d = p->d;
+    L.k = p->k;
+    L.rule = p->rule;
+    L.seed = p->seed;
+    L.scale = p->scale;
+    cudaError_t e = launch_literal(L, st, launches);
+    if (e != cudaSuccess) return cuda_fail(e, "literal kernel launch");
+    if (R_used) *R_used = 1;
+    return SK_OK;
+  }
+  TileCfg cfg;
+  s = choose_tile(p, n, p->m, di, &cfg);
+  if (s != SK_OK) return s;
+  if (R_fixed > 0) cfg.R = R_fixed;
+  TileLaunch L;
+  L.A = A;
+  L.Y = Y;
+  L.lda = lda;
+  L.n = n;
+  L.row_begin = row_begin;
+  L.row_end = row_end;
+  L.d = p->d;
+  L.k = p->k;
+  L.rule = p->rule;
+  L.seed = p->seed;
+  L.scale = p->scale;
+  L.R = cfg.R;
+  L.NC = cfg.NC;
+  L.kb = cfg.kb;
+  L.threads = cfg.threads;
+  L.grid = cfg.grid;
+  cudaError_t e = launch_tile(L, st, launches);
+  if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");
+  if (R_used) *R_used = cfg.R;
+  return SK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t sk_version(void) { return 10000; }
+
+const char* sk_last_error(void) { return last_error_message(); }
+
+sk_status sk_plan_create(int64_t d, int64_t m, int32_t k, int32_t rule, uint64_t seed, sk_plan* out) {
+  clear_error();
+  if (!out) return set_error(SK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (k < 1 || k > kMaxK) return set_error(SK_ERR_INVALID_ARG, "k=%d outside [1, %d]", k, kMaxK);
+  if (d < 1 || d % k != 0) return set_error(SK_ERR_INVALID_ARG, "d=%lld must be a positive multiple of k=%d", (long long)d, k);
+  if (d > 0x7fffffffLL) return set_error(SK_ERR_UNSUPPORTED, "d=%lld above 2^31-1", (long long)d);
+  if (m < 1) return set_error(SK_ERR_INVALID_ARG, "m=%lld must be >= 1", (long long)m);
+  if (m > ((int64_t)1 << 56)) return set_error(SK_ERR_UNSUPPORTED, "m=%lld too large", (long long)m);
+  if (rule < SK_FP32 || rule > SK_FP16_DITHER) return set_error(SK_ERR_INVALID_ARG, "unknown rule %d", rule);
+  sk_plan_s* p = new (std::nothrow) sk_plan_s();
+  if (!p) return set_error(SK_ERR_OOM, "host allocation failed");
+  p->d = d;
+  p->m = m;
+  p->k = k;
+  p->B = d / k;
+  p->rule = rule;
+  p->seed = seed;
+  p->scale = (float)(1.0 / std::sqrt((double)k));
+  *out = p;
+  return SK_OK;
+}
+
+sk_status sk_plan_set(sk_plan p, int32_t key, int64_t v) {
+  clear_error();
+  if (!p) return set_error(SK_ERR_INVALID_ARG, "plan is NULL");
+  switch (key) {
+    case SK_PARAM_CHUNK_ROWS:
+      if (v < 0) return set_error(SK_ERR_INVALID_ARG, "chunk rows must be >= 0");
+      p->R = v;
+      return SK_OK;
+    case SK_PARAM_MODE:
+      if (v < 0 || v > 2) return set_error(SK_ERR_INVALID_ARG, "mode must be 0 (atomic), 1 (deterministic) or 2 (serial tile)");
+      p->mode = (int32_t)v;
+      return SK_OK;
+    case SK_PARAM_ROW_OFFSET:
+      if (v < 0) return set_error(SK_ERR_INVALID_ARG, "row offset must be >= 0");
+      p->row_offset = v;
+      return SK_OK;
+    case SK_PARAM_KERNEL:
+      if (v < SK_KERNEL_AUTO || v > SK_KERNEL_LITERAL) return set_error(SK_ERR_INVALID_ARG, "unknown kernel %lld", (long long)v);
+      p->kernel = (int32_t)v;
+      return SK_OK;
+    case SK_PARAM_TILE_COLS:
+      if (v != 0 && v != 4 && v != 8 && v != 16 && v != 32)
+        return set_error(SK_ERR_INVALID_ARG, "tile cols must be 0, 4, 8, 16 or 32");
+      p->tile_cols = (int32_t)v;
+      return SK_OK;
+    case SK_PARAM_THREADS:
+      if (v != 0 && (v < 128 || v > 1024 || v % 32 != 0))
+        return set_error(SK_ERR_INVALID_ARG, "threads must be 0 or a multiple of 32 in [128, 1024]");
+      p->threads = (int32_t)v;
+      return SK_OK;
+    default:
+      return set_error(SK_ERR_INVALID_ARG, "unknown or read-only key %d", key);
+  }
+}
+
+sk_status sk_plan_get(sk_plan p, int32_t key, int64_t* v) {
+  clear_error();
+  if (!p || !v) return set_error(SK_ERR_INVALID_ARG, "NULL argument");
+  switch (key) {
+    case SK_PARAM_CHUNK_ROWS: *v = p->R; return SK_OK;
+    case SK_PARAM_MODE: *v = p->mode; return SK_OK;
+    case SK_PARAM_ROW_OFFSET: *v = p->row_offset; return SK_OK;
+    case SK_PARAM_KERNEL: *v = p->kernel; return SK_OK;
+    case SK_PARAM_TILE_COLS: *v = p->tile_cols; return SK_OK;
+    case SK_PARAM_THREADS: *v = p->threads; return SK_OK;
+    case SK_PARAM_LAST_LAUNCHES: *v = p->last_launches; return SK_OK;
+    case SK_PARAM_LAST_CHUNK_ROWS: *v = p->last_R; return SK_OK;
+    default: return set_error(SK_ERR_INVALID_ARG, "unknown key %d", key);
+  }
+}
+
+sk_status sk_apply(sk_plan p, const float* A, int64_t lda, int64_t n, void* Y, void* stream) {
+  clear_error();
+  sk_status s = validate_apply(p, A, lda, n, Y);
+  if (s != SK_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t launches = 0;
+  cudaError_t e = cudaMemsetAsync(Y, 0, elem_size(p->rule) * (size_t)(p->d * n), st);
+  if (e != cudaSuccess) return cuda_fail(e, "zeroing Y");
+  int64_t R_used = 0;
+  s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, Y, 0, st, &launches, &R_used);
+  p->last_launches = launches;
+  p->last_R = R_used;
+  return s;
+}
+
+sk_status sk_apply_host(sk_plan p, const float* A_host, int64_t lda, int64_t n, void* Y_host, void* stream) {
+  clear_error();
+  sk_status s = validate_apply(p, A_host, lda, n, Y_host);
+  if (s != SK_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevInfo di;
+  s = dev_info(&di);
+  if (s != SK_OK) return s;
+  // Chunk rows of the whole matrix, so that the tiles reproduce sk_apply's chunks exactly.
+  int64_t R = p->R;
+  if (p->kernel == SK_KERNEL_LITERAL) R = 1;
+  if (R <= 0) {
+    TileCfg cfg;
+    s = choose_tile(p, n, p->m, di, &cfg);
+    if (s != SK_OK) return s;
+    R = cfg.R;
+  }
+  // Tiles of whole chunks, about 128 MiB each.
+  const int64_t row_bytes = lda * 4;
+  const int64_t target_rows = std::max<int64_t>(1, ((int64_t)128 << 20) / row_bytes);
+  int64_t tile_rows;
+  if (R >= target_rows) {
+    tile_rows = R;
+  } else {
+    tile_rows = (target_rows / R) * R;
+  }
+  // The first chunk may be partial when the row offset is not a multiple of R: align tiles to the
+  // global chunk grid.
+  tile_rows = std::min(tile_rows, p->m + (p->row_offset % R));
+  const size_t tile_bytes = (size_t)tile_rows * (size_t)row_bytes;
+  const size_t ybytes = elem_size(p->rule) * (size_t)(p->d * n);
+  if (p->stage_bytes < tile_bytes) {
+    for (int b = 0; b < 2; ++b) {
+      if (p->stage[b]) cudaFree(p->stage[b]);
+      p->stage[b] = nullptr;
+    }
+    p->stage_bytes = 0;
+    for (int b = 0; b < 2; ++b) {
+      if (cudaMalloc(&p->stage[b], tile_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SK_ERR_OOM, "host pipeline staging (%zu bytes)", tile_bytes);
+      }
+    }
+    p->stage_bytes = tile_bytes;
+  }
+  if (p->ydev_bytes < ybytes) {
+    if (p->ydev) cudaFree(p->ydev);
+    p->ydev = nullptr;
+    p->ydev_bytes = 0;
+    if (cudaMalloc(&p->ydev, ybytes) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(SK_ERR_OOM, "host pipeline Y buffer (%zu bytes)", ybytes);
+    }
+    p->ydev_bytes = ybytes;
+  }
+  if (!p->copy_stream) {
+    if (cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cuda_fail(cudaGetLastError(), "copy stream");
+    for (int b = 0; b < 2; ++b) {
+      cudaEventCreateWithFlags(&p->ev_copied[b], cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&p->ev_used[b], cudaEventDisableTiming);
+    }
+  }
+  int32_t launches = 0;
+  cudaError_t e = cudaMemsetAsync(p->ydev, 0, ybytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "zeroing Y");
+  // Buffers start free: mark both as used-and-finished on the compute stream.
+  for (int b = 0; b < 2; ++b) cudaEventRecord(p->ev_used[b], st);
+  int64_t done = 0;
+  int which = 0;
+  const int64_t g0 = p->row_offset;
+  while (done < p->m) {
+    // Tile boundaries on the global chunk grid.
+    const int64_t gstart = g0 + done;
+    const int64_t chunk_start = (gstart / R) * R;
+    int64_t gend = chunk_start + tile_rows;
+    if (gend <= gstart) gend = gstart + R;
+    gend = std::min(gend, g0 + p->m);
+    const int64_t rows = gend - gstart;
+    float* buf = p->stage[which];
+    e = cudaStreamWaitEvent(p->copy_stream, p->ev_used[which], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline wait");
+    if (lda == n) {
+      e = cudaMemcpyAsync(buf, A_host + done * lda, (size_t)rows * n * 4, cudaMemcpyHostToDevice, p->copy_stream);
+    } else {
+      e = cudaMemcpy2DAsync(buf, (size_t)lda * 4, A_host + done * lda, (size_t)lda * 4, (size_t)n * 4, (size_t)rows,
+                            cudaMemcpyHostToDevice, p->copy_stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
+    cudaEventRecord(p->ev_copied[which], p->copy_stream);
+    cudaStreamWaitEvent(st, p->ev_copied[which], 0);
+    s = enqueue_sketch(p, buf, lda, n, gstart, rows, p->ydev, R, st, &launches, nullptr);
+    if (s != SK_OK) return s;
+    cudaEventRecord(p->ev_used[which], st);
+    done += rows;
+    which ^= 1;
+  }
+  e = cudaMemcpyAsync(Y_host, p->ydev, ybytes, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "sk_apply_host");
+  p->last_launches = launches;
+  p->last_R = R;
+  return SK_OK;
+}
+
+sk_status sk_materialize_S(sk_plan p, int64_t i0, int64_t cnt, int32_t* rows, int8_t* signs, void* stream) {
+  clear_error();
+  if (!p || !rows || !signs) return set_error(SK_ERR_INVALID_ARG, "NULL argument");
+  if (i0 < 0 || cnt < 0) return set_error(SK_ERR_INVALID_ARG, "negative range");
+  if (cnt == 0) return SK_OK;
+  cudaError_t e = launch_pattern(p->d, p->k, p->seed, i0, cnt, rows, signs, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pattern kernel launch");
+  return SK_OK;
+}
+
+// Solve scratch layout (bytes, each region 256-byte aligned):
+//   Y_A (d*n elements), Y_b (d elements), part (n + n*(n+1) doubles), R (n*(n+1) doubles),
+//   bcast (n doubles), bar (2 words), status (1 word), kappa (1 double).
+namespace {
+struct SolveLayout {
+  size_t ya, yb, part, R, bcast, bar, status, kappa, total;
+};
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+SolveLayout solve_layout(int64_t d, int64_t n, int32_t rule) {
+  SolveLayout L;
+  size_t off = 0;
+  const size_t es = elem_size(rule);
+  L.ya = off; off = al256(off + es * (size_t)(d * n));
+  L.yb = off; off = al256(off + es * (size_t)d);
+  L.part = off; off = al256(off + 8 * (size_t)(n + n * (n + 1)));
+  L.R = off; off = al256(off + 8 * (size_t)(n * (n + 1)));
+  L.bcast = off; off = al256(off + 8 * (size_t)n);
+  L.bar = off; off = al256(off + 8);
+  L.status = off; off = al256(off + 4);
+  L.kappa = off; off = al256(off + 8);
+  L.total = off;
+  return L;
+}
+}  // namespace
+
+sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const float* b, float* x, void* stream) {
+  clear_error();
+  sk_status s = validate_apply(p, A, lda, n, x);
+  if (s != SK_OK) return s;
+  if (!b) return set_error(SK_ERR_INVALID_ARG, "b is NULL");
+  if (n > p->d) return set_error(SK_ERR_INVALID_ARG, "sketch-and-solve needs n=%lld <= d=%lld", (long long)n, (long long)p->d);
+  if (n > kMaxSolveN) return set_error(SK_ERR_UNSUPPORTED, "sketch-and-solve supports n <= %d", kMaxSolveN);
+  DevInfo di;
+  s = dev_info(&di);
+  if (s != SK_OK) return s;
+  const int32_t ncta = solve_ctas(p->d, n, di.sms, (size_t)di.optin);
+  if (ncta < 1) return set_error(SK_ERR_UNSUPPORTED, "FP64 QR of a %lld x %lld sketch does not fit", (long long)p->d, (long long)(n + 1));
+  const SolveLayout Lo = solve_layout(p->d, n, p->rule);
+  if (p->solve_bytes < Lo.total) {
+    if (p->solve_buf) cudaFree(p->solve_buf);
+    p->solve_buf = nullptr;
+    p->solve_bytes = 0;
+    if (cudaMalloc(&p->solve_buf, Lo.total) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(SK_ERR_OOM, "sketch-and-solve scratch (%zu bytes)", Lo.total);
+    }
+    cudaMemset(p->solve_buf, 0, Lo.total);
+    p->solve_bytes = Lo.total;
+  }
+  p->solve_status_off = Lo.status;
+  p->solve_kappa_off = Lo.kappa;
+  char* base = (char*)p->solve_buf;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t launches = 0;
+  const size_t es = elem_size(p->rule);
+  cudaError_t e = cudaMemsetAsync(base + Lo.ya, 0, Lo.part - Lo.ya, st);  // Y_A and Y_b
+  if (e != cudaSuccess) return cuda_fail(e, "zeroing sketches");
+  e = cudaMemsetAsync(base + Lo.status, 0, 4, st);
+  if (e != cudaSuccess) return cuda_fail(e, "zeroing status");
+  (void)es;
+  int64_t R_used = 0;
+  s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, base + Lo.ya, 0, st, &launches, &R_used);
+  if (s != SK_OK) return s;
+  s = enqueue_sketch(p, b, 1, 1, p->row_offset, p->m, base + Lo.yb, R_used, st, &launches, nullptr);
+  if (s != SK_OK) return s;
+  SolveLaunch L;
+  L.SA = base + Lo.ya;
+  L.Sb = base + Lo.yb;
+  L.rule = p->rule;
+  L.d = p->d;
+  L.n = n;
+  L.part = (double*)(base + Lo.part);
+  L.R = (double*)(base + Lo.R);
+  L.bcast = (double*)(base + Lo.bcast);
+  L.bar = (unsigned*)(base + Lo.bar);
+  L.status = (unsigned*)(base + Lo.status);
+  L.kappa = (double*)(base + Lo.kappa);
+  L.x = x;
+  L.ncta = ncta;
+  e = launch_solve(L, st, &launches);
+  if (e != cudaSuccess) return cuda_fail(e, "QR launch");
+  p->last_launches = launches;
+  p->last_R = R_used;
+  return SK_OK;
+}
+
+sk_status sk_solve_status(sk_plan p, double* kappa, void* stream) {
+  clear_error();
+  if (!p) return set_error(SK_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->solve_buf) return set_error(SK_ERR_INVALID_ARG, "no sk_solve has run on this plan");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "sk_solve_status");
+  unsigned status = 0;
+  double kap = 0.0;
+  e = cudaMemcpy(&status, (char*)p->solve_buf + p->solve_status_off, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "reading solve status");
+  e = cudaMemcpy(&kap, (char*)p->solve_buf + p->solve_kappa_off, 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "reading kappa");
+  if (kappa) *kappa = kap;
+  if (status & 1u) return set_error(SK_ERR_TIMEOUT, "a grid barrier of the QR kernel timed out");
+  if (status & 2u) return set_error(SK_ERR_NUMERIC, "SA is rank deficient (zero pivot in the QR)");
+  return SK_OK;
+}
+
+void sk_destroy(sk_plan p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  if (p->det_P) cudaFree(p->det_P);
+  if (p->solve_buf) cudaFree(p->solve_buf);
+  for (int b = 0; b < 2; ++b) {
+    if (p->stage[b]) cudaFree(p->stage[b]);
+    if (p->ev_copied[b]) cudaEventDestroy(p->ev_copied[b]);
+    if (p->ev_used[b]) cudaEventDestroy(p->ev_used[b]);
+  }
+  if (p->ydev) cudaFree(p->ydev);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,380 @@
+// Batched uneven sketches in one persistent launch. Every matrix of the batch is cut into work
+// items (chunk of rows x column group x block group), the items of all matrices are sorted by cost
+// (largest first) into one device work list, and resident CTAs take items from it through an atomic
+// counter until it is exhausted. The per-item processing is the tile scatter/flush of the
+// single-matrix kernel (paper Sec. 4.1-4.2 with on-chip chunk accumulation).
+//
+// sk_batch_launch enqueues exactly two kernels (zero every Y_i and reset the counter; then the
+// persistent kernel), allocates nothing and never synchronizes, so it can be captured in a CUDA
+// graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/sk.h"
+#include "sk_device.cuh"
+#include "sk_hostutil.h"
+#include "sk_internal.h"
+#include "sk_tile.cuh"
+
+namespace sk {
+
+struct BatchDesc {
+  TileDesc D;
+  int64_t R;
+};
+
+struct BatchWork {
+  int64_t r0, r1, t;
+  int32_t item, g, j0, kbe;
+};
+
+struct ZeroSpan {
+  void* p;
+  int64_t bytes;
+};
+
+__global__ void batch_zero_kernel(const ZeroSpan* spans, int32_t nspan, int32_t* counter) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+  for (int32_t s = blockIdx.y; s < nspan; s += gridDim.y) {
+    const ZeroSpan z = spans[s];
+    // spans are 4-byte aligned and sized (d x n floats or d x n halves padded to 4 bytes)
+    uint32_t* p = reinterpret_cast<uint32_t*>(z.p);
+    const int64_t words = z.bytes >> 2;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < words; x += (int64_t)gridDim.x * blockDim.x)
+      p[x] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (z.bytes & 3)) {
+      reinterpret_cast<uint16_t*>(z.p)[(z.bytes >> 1) - 1] = 0;
+    }
+  }
+}
+
+template <int RULE>
+__global__ void __launch_bounds__(1024) batch_kernel(const BatchDesc* __restrict__ descs,
+                                                     const BatchWork* __restrict__ work, int64_t nwork,
+                                                     int32_t* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t next;
+  __shared__ BatchDesc dsh;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  float* acc = reinterpret_cast<float*>(smem_raw);
+  // The accumulator takes the dynamic shared memory minus the per-warp stream buffers at its end.
+  uint32_t dyn = 0;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  const uint32_t hbytes = (uint32_t)nwarps * 32u * 8u;
+  uint64_t* hbuf = reinterpret_cast<uint64_t*>(smem_raw + (dyn - hbytes)) + warp * 32;
+  const int64_t acc_floats = (int64_t)(dyn - hbytes) / 4;
+  for (int64_t x = threadIdx.x; x < acc_floats; x += blockDim.x) acc[x] = 0.f;
+  __syncthreads();
+  while (true) {
+    if (threadIdx.x == 0) next = (int64_t)atomicAdd(counter, 1);
+    __syncthreads();
+    const int64_t w = next;
+    if (w >= nwork) break;
+    const BatchWork wk = work[w];
+    if (threadIdx.x == 0) dsh = descs[wk.item];
+    __syncthreads();
+    tile_scatter(dsh.D, wk.r0, wk.r1, wk.g, wk.j0, wk.kbe, acc, hbuf, warp, nwarps);
+    __syncthreads();
+    tile_flush<RULE>(dsh.D, wk.t, wk.g, wk.j0, wk.kbe, acc);
+    __threadfence();
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_batch(const void* descs, const void* work, int64_t nwork, int32_t* counter, const void* zero_list,
+                         int32_t nzero, int32_t rule, int32_t threads, size_t smem, int32_t grid, cudaStream_t st,
+                         int32_t* launches) {
+  dim3 zg(64, (unsigned)std::min(nzero, 1024));
+  batch_zero_kernel<<<zg, 256, 0, st>>>(reinterpret_cast<const ZeroSpan*>(zero_list), nzero, counter);
+  if (launches) *launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const BatchDesc* dd = reinterpret_cast<const BatchDesc*>(descs);
+  const BatchWork* ww = reinterpret_cast<const BatchWork*>(work);
+  switch (rule) {
+    case kRN: batch_kernel<kRN><<<grid, threads, smem, st>>>(dd, ww, nwork, counter); break;
+    case kSR: batch_kernel<kSR><<<grid, threads, smem, st>>>(dd, ww, nwork, counter); break;
+    case kDither: batch_kernel<kDither><<<grid, threads, smem, st>>>(dd, ww, nwork, counter); break;
+    default: batch_kernel<kFP32><<<grid, threads, smem, st>>>(dd, ww, nwork, counter); break;
+  }
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+static const void* batch_kernel_ptr(int rule) {
+  switch (rule) {
+    case kRN: return (const void*)batch_kernel<kRN>;
+    case kSR: return (const void*)batch_kernel<kSR>;
+    case kDither: return (const void*)batch_kernel<kDither>;
+    default: return (const void*)batch_kernel<kFP32>;
+  }
+}
+
+}  // namespace sk
+
+using namespace sk;
+
+struct sk_batch_s {
+  std::vector<sk_batch_item> items;
+  int32_t rule = 0;
+  int32_t threads = 0, tile_cols = 0;
+  int64_t chunk_rows = 0;
+  bool built = false;
+  int device = 0;
+  // device state
+  BatchDesc* d_descs = nullptr;
+  BatchWork* d_work = nullptr;
+  ZeroSpan* d_zero = nullptr;
+  int32_t* d_counter = nullptr;
+  int64_t nwork = 0;
+  int64_t bytes_A = 0;
+  size_t smem = 0;
+  int32_t grid = 0, use_threads = 0;
+};
+
+namespace {
+
+void free_batch_dev(sk_batch_s* b) {
+  if (b->d_descs) cudaFree(b->d_descs);
+  if (b->d_work) cudaFree(b->d_work);
+  if (b->d_zero) cudaFree(b->d_zero);
+  if (b->d_counter) cudaFree(b->d_counter);
+  b->d_descs = nullptr;
+  b->d_work = nullptr;
+  b->d_zero = nullptr;
+  b->d_counter = nullptr;
+}
+
+// Build the work list and upload it (called on the first launch so that overrides apply).
+sk_status build_batch(sk_batch_s* b) {
+  int dev = 0, sms = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return set_error(SK_ERR_CUDA, "cudaGetDevice failed");
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  b->device = dev;
+  const int32_t threads = b->threads > 0 ? b->threads : 1024;
+  const size_t hbytes = (size_t)(threads / 32) * 32 * 8;
+  const size_t budget = (size_t)std::min(optin, 232448) - hbytes - 1024;
+  const size_t budget_floats = budget / 4;
+  const int32_t count = (int32_t)b->items.size();
+  std::vector<BatchDesc> descs(count);
+  std::vector<int32_t> ncgs(count), nbgs(count);
+  size_t max_floats = 0;
+  double total_cost = 0.0;
+  for (int32_t i = 0; i < count; ++i) {
+    const sk_batch_item& it = b->items[i];
+    const int64_t B = it.d / it.k;
+    // Widest column group (not wider than needed) whose accumulator holds all k blocks; if none
+    // does, the narrowest allowed width with as many blocks per group as fit.
+    int32_t NC = 0, kb = 0;
+    const int32_t widths[4] = {32, 16, 8, 4};
+    for (int32_t c : widths) {
+      if (b->tile_cols > 0 && c != b->tile_cols) continue;
+      if (c > 4 && c / 2 >= it.n) continue;
+      if ((size_t)tile_acc_floats((uint32_t)B, it.k, tile_slots(c, it.k), c) <= budget_floats) {
+        NC = c;
+        kb = it.k;
+        break;
+      }
+    }
+    if (NC == 0) {
+      NC = b->tile_cols > 0 ? b->tile_cols : 4;
+      for (int32_t kbt = it.k; kbt >= 1; --kbt) {
+        if ((size_t)tile_acc_floats((uint32_t)B, kbt, tile_slots(NC, kbt), NC) <= budget_floats) {
+          kb = kbt;
+          break;
+        }
+      }
+    }
+    if (kb == 0)
+      return set_error(SK_ERR_UNSUPPORTED, "batch item %d: a block of %lld rows does not fit in shared memory", i,
+                       (long long)B);
+    BatchDesc& D = descs[i];
+    D.D.A = it.A_dev;
+    D.D.Y = it.Y_dev;
+    D.D.lda = it.lda;
+    D.D.n = it.n;
+    D.D.row_base = 0;
+    D.D.seed = it.seed;
+    D.D.scale = (float)(1.0 / std::sqrt((double)it.k));
+    D.D.B = (uint32_t)B;
+    D.D.k = (uint32_t)it.k;
+    D.D.kp = (uint32_t)((it.k + 1) / 2);
+    int l2 = 0;
+    while ((1 << l2) < NC) ++l2;
+    D.D.log2NC = l2;
+    D.D.S = tile_slots(NC, kb);
+    D.D.kb = kb;
+    ncgs[i] = (int32_t)((it.n + NC - 1) / NC);
+    nbgs[i] = (it.k + kb - 1) / kb;
+    max_floats = std::max(max_floats, (size_t)tile_acc_floats((uint32_t)B, kb, D.D.S, NC));
+    total_cost += (double)it.m * (double)ncgs[i] * NC * it.k;
+  }
+  // Chunk rows: aim at ~4 work items per CTA slot over the whole batch, and at most 32 chunks per
+  // matrix (each output then receives at most 32 rounded contributions).
+  const double target_cost = total_cost / (4.0 * sms);
+  std::vector<BatchWork> work;
+  b->bytes_A = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    const sk_batch_item& it = b->items[i];
+    const int32_t NC = 1 << descs[i].D.log2NC;
+    int64_t R;
+    if (b->chunk_rows > 0) {
+      R = b->chunk_rows;
+    } else {
+      const double per_row = (double)ncgs[i] * NC * it.k;
+      R = (int64_t)std::ceil(target_cost / std::max(per_row, 1.0));
+      R = std::max<int64_t>(R, (it.m + 31) / 32);
+      R = std::max<int64_t>(R, 256);
+      R = ((R + 255) / 256) * 256;
+    }
+    descs[i].R = R;
+    b->bytes_A += it.m * it.n * 4;
+    const int64_t nch = (it.m + R - 1) / R;
+    for (int64_t t = 0; t < nch; ++t)
+      for (int32_t bg = 0; bg < nbgs[i]; ++bg)
+        for (int32_t g = 0; g < ncgs[i]; ++g) {
+          BatchWork w;
+          w.r0 = t * R;
+          w.r1 = std::min((t + 1) * R, it.m);
+          w.t = t;
+          w.item = i;
+          w.g = g;
+          w.j0 = bg * descs[i].D.kb;
+          w.kbe = std::min(descs[i].D.kb, it.k - w.j0);
+          work.push_back(w);
+        }
+  }
+  // Largest first.
+  std::stable_sort(work.begin(), work.end(), [&](const BatchWork& x, const BatchWork& y) {
+    const double cx = (double)(x.r1 - x.r0) * x.kbe * (1 << descs[x.item].D.log2NC);
+    const double cy = (double)(y.r1 - y.r0) * y.kbe * (1 << descs[y.item].D.log2NC);
+    return cx > cy;
+  });
+  std::vector<ZeroSpan> zs(count);
+  for (int32_t i = 0; i < count; ++i) {
+    const int64_t es = (b->rule == SK_FP32) ? 4 : 2;
+    zs[i].p = b->items[i].Y_dev;
+    zs[i].bytes = b->items[i].d * b->items[i].n * es;
+  }
+  free_batch_dev(b);
+  if (cudaMalloc(&b->d_descs, sizeof(BatchDesc) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_work, sizeof(BatchWork) * std::max<size_t>(work.size(), 1)) != cudaSuccess ||
+      cudaMalloc(&b->d_zero, sizeof(ZeroSpan) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_counter, sizeof(int32_t)) != cudaSuccess) {
+    free_batch_dev(b);
+    cudaGetLastError();
+    return set_error(SK_ERR_OOM, "batch work list allocation failed");
+  }
+  cudaMemcpy(b->d_descs, descs.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice);
+  if (!work.empty()) cudaMemcpy(b->d_work, work.data(), sizeof(BatchWork) * work.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_zero, zs.data(), sizeof(ZeroSpan) * count, cudaMemcpyHostToDevice);
+  cudaMemset(b->d_counter, 0, sizeof(int32_t));
+  b->nwork = (int64_t)work.size();
+  b->smem = max_floats * 4 + hbytes;
+  b->use_threads = threads;
+  const void* kern = batch_kernel_ptr(b->rule);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) != cudaSuccess)
+    return set_error(SK_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(cudaGetLastError()));
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (void (*)(const BatchDesc*, const BatchWork*, int64_t, int32_t*))kern,
+                                                threads, b->smem);
+  if (per_sm < 1) return set_error(SK_ERR_UNSUPPORTED, "batch kernel does not fit on an SM");
+  b->grid = (int32_t)std::min<int64_t>((int64_t)sms * per_sm, std::max<int64_t>(b->nwork, 1));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "batch build: %s", cudaGetErrorString(e));
+  b->built = true;
+  return SK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sk_status sk_batch_create(const sk_batch_item* items, int32_t count, int32_t rule, sk_batch* out) {
+  clear_error();
+  if (!out) return set_error(SK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!items || count < 1) return set_error(SK_ERR_INVALID_ARG, "need at least one item");
+  if (rule < SK_FP32 || rule > SK_FP16_DITHER) return set_error(SK_ERR_INVALID_ARG, "unknown rule %d", rule);
+  for (int32_t i = 0; i < count; ++i) {
+    const sk_batch_item& it = items[i];
+    if (!it.A_dev || !it.Y_dev) return set_error(SK_ERR_INVALID_ARG, "item %d: NULL pointer", i);
+    if (it.m < 1 || it.n < 1 || it.n > 65535 || it.lda < it.n || it.d < 1 || it.k < 1 || it.k > 64 ||
+        it.d % it.k != 0)
+      return set_error(SK_ERR_INVALID_ARG, "item %d: invalid sizes (m=%lld n=%lld lda=%lld d=%lld k=%d)", i,
+                       (long long)it.m, (long long)it.n, (long long)it.lda, (long long)it.d, it.k);
+    if ((reinterpret_cast<uintptr_t>(it.Y_dev) & 3u) != 0)
+      return set_error(SK_ERR_INVALID_ARG, "item %d: Y must be 4-byte aligned", i);
+    if (it.d / it.k > 0x7fffffffLL) return set_error(SK_ERR_UNSUPPORTED, "item %d: block too large", i);
+  }
+  sk_batch_s* b = new (std::nothrow) sk_batch_s();
+  if (!b) return set_error(SK_ERR_OOM, "host allocation failed");
+  b->items.assign(items, items + count);
+  b->rule = rule;
+  *out = b;
+  return SK_OK;
+}
+
+sk_status sk_batch_set(sk_batch b, int32_t key, int64_t value) {
+  clear_error();
+  if (!b) return set_error(SK_ERR_INVALID_ARG, "batch is NULL");
+  if (b->built) return set_error(SK_ERR_INVALID_ARG, "batch already launched; set parameters before the first launch");
+  switch (key) {
+    case SK_PARAM_TILE_COLS:
+      if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32)
+        return set_error(SK_ERR_INVALID_ARG, "tile cols must be 0, 4, 8, 16 or 32");
+      b->tile_cols = (int32_t)value;
+      return SK_OK;
+    case SK_PARAM_THREADS:
+      if (value != 0 && (value < 128 || value > 1024 || value % 32 != 0))
+        return set_error(SK_ERR_INVALID_ARG, "threads must be 0 or a multiple of 32 in [128, 1024]");
+      b->threads = (int32_t)value;
+      return SK_OK;
+    case SK_PARAM_CHUNK_ROWS:
+      if (value < 0) return set_error(SK_ERR_INVALID_ARG, "chunk rows must be >= 0");
+      b->chunk_rows = value;
+      return SK_OK;
+    default:
+      return set_error(SK_ERR_INVALID_ARG, "unknown batch key %d", key);
+  }
+}
+
+sk_status sk_batch_launch(sk_batch b, void* stream) {
+  clear_error();
+  if (!b) return set_error(SK_ERR_INVALID_ARG, "batch is NULL");
+  if (!b->built) {
+    sk_status s = build_batch(b);
+    if (s != SK_OK) return s;
+  }
+  int32_t launches = 0;
+  cudaError_t e = launch_batch(b->d_descs, b->d_work, b->nwork, b->d_counter, b->d_zero, (int32_t)b->items.size(),
+                               b->rule, b->use_threads, b->smem, b->grid, (cudaStream_t)stream, &launches);
+  if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
+  return SK_OK;
+}
+
+sk_status sk_batch_info(sk_batch b, int64_t* work_items, int64_t* bytes_A) {
+  clear_error();
+  if (!b) return set_error(SK_ERR_INVALID_ARG, "batch is NULL");
+  if (!b->built) {
+    sk_status s = build_batch(b);
+    if (s != SK_OK) return s;
+  }
+  if (work_items) *work_items = b->nwork;
+  if (bytes_A) *bytes_A = b->bytes_A;
+  return SK_OK;
+}
+
+void sk_batch_destroy(sk_batch b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  free_batch_dev(b);
+  delete b;
+}
+
+}  // extern "C"

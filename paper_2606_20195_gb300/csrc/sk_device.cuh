@@ -1,0 +1,113 @@
+// Device primitives of the sketch kernels: the counter-based S generator, Philox4x32-10 for the
+// rounding bits, and the three FP16 quantizers of paper Sec. 4.2.
+//
+// Every FP32 operation whose rounding matters is written with an explicit _rn intrinsic so that
+// nvcc cannot contract it into an FMA: the deterministic modes must reproduce the canonical order
+// bit for bit.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace sk {
+
+// ------------------------------------------------------------------ SplitMix64
+// Steele, Lea & Flood, "Fast splittable pseudorandom number generators" (OOPSLA 2014): the state
+// advances by the golden-ratio increment and each output is the state passed through the 64-bit
+// finalizer below.
+__device__ __forceinline__ uint64_t splitmix_finalize(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+
+// Output number `idx` (idx >= 1) of the SplitMix64 stream started at `seed`.
+__device__ __forceinline__ uint64_t splitmix_output(uint64_t seed, uint64_t idx) {
+  return splitmix_finalize(seed + idx * 0x9E3779B97F4A7C15ull);
+}
+
+// The 64 bits serving blocks 2p and 2p+1 of input row i: stream output i*kp + p + 1, kp = ceil(k/2).
+__device__ __forceinline__ uint64_t row_pair_bits(uint64_t seed, uint64_t i, uint32_t kp, uint32_t p) {
+  return splitmix_output(seed, i * (uint64_t)kp + (uint64_t)p + 1ull);
+}
+
+// 32-bit word of block j from the 64 bits of its block pair: even j -> high half, odd j -> low half.
+__device__ __forceinline__ uint32_t block_word(uint64_t bits, uint32_t j) {
+  return (j & 1u) ? (uint32_t)bits : (uint32_t)(bits >> 32);
+}
+
+// Row offset inside block j (0 <= s < B) from the block's word: Lemire's multiply-shift,
+// floor(w * B / 2^32). Sign bit: bit 0 of the word (1 -> negative).
+__device__ __forceinline__ uint32_t word_to_slot(uint32_t w, uint32_t B) { return __umulhi(w, B); }
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11).
+struct u32x4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ u32x4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                          uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo_a = 0xD2511F53u * c0;
+    const uint32_t hi_a = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo_b = 0xCD9E8D57u * c2;
+    const uint32_t hi_b = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi_b ^ c1 ^ k0;
+    const uint32_t n2 = hi_a ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo_b;
+    c2 = n2;
+    c3 = lo_a;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return {c0, c1, c2, c3};
+}
+
+// Four uniforms in [0,1) for output row r, columns 4q..4q+3, contribution t. The key is the seed,
+// the counter (r, q, lo32 t, hi32 t). Each uses the low 24 bits of its word times 2^-24.
+__device__ __forceinline__ void uniforms4(uint64_t seed, uint32_t r, uint32_t q, uint64_t t, float u[4]) {
+  const u32x4 w = philox10(r, q, (uint32_t)t, (uint32_t)(t >> 32), (uint32_t)seed, (uint32_t)(seed >> 32));
+  const float s = 5.9604644775390625e-08f;  // 2^-24
+  u[0] = __fmul_rn(__uint2float_rn(w.x & 0xFFFFFFu), s);
+  u[1] = __fmul_rn(__uint2float_rn(w.y & 0xFFFFFFu), s);
+  u[2] = __fmul_rn(__uint2float_rn(w.z & 0xFFFFFFu), s);
+  u[3] = __fmul_rn(__uint2float_rn(w.w & 0xFFFFFFu), s);
+}
+
+// ------------------------------------------------------------------ FP16 quantizers (paper Sec. 4.2)
+enum Rule : int { kFP32 = 0, kRN = 1, kSR = 2, kDither = 3 };
+
+// Exact stochastic rounding: upper neighbour with probability (x - rd) / (ru - rd).
+__device__ __forceinline__ __half quant_sr(float x, float u) {
+  const __half lo = __float2half_rd(x);
+  const __half hi = __float2half_ru(x);
+  const float flo = __half2float(lo);
+  const float span = __fsub_rn(__half2float(hi), flo);
+  const float off = __fsub_rn(x, flo);
+  return (__fmul_rn(u, span) < off) ? hi : lo;
+}
+
+// Non-subtractive dither: zero-mean uniform noise of amplitude x * 2^-10 (about one binary16 ulp),
+// then round to nearest even.
+__device__ __forceinline__ __half quant_dither(float x, float u) {
+  const float noise = __fmul_rn(__fsub_rn(u, 0.5f), __fmul_rn(x, 0.0009765625f));
+  return __float2half_rn(__fadd_rn(x, noise));
+}
+
+template <int RULE>
+__device__ __forceinline__ __half quantize(float x, float u) {
+  if (RULE == kSR) return quant_sr(x, u);
+  if (RULE == kDither) return quant_dither(x, u);
+  return __float2half_rn(x);
+}
+
+// Status word bits written by kernels that detect a problem (never trap).
+enum : unsigned { kStatusTimeout = 1u, kStatusNumeric = 2u, kStatusBounds = 4u };
+
+}  // namespace sk

@@ -1,0 +1,81 @@
+// Internal launch interfaces shared by the translation units of libsk (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sk {
+
+struct TileLaunch {
+  const float* A;
+  void* Y;
+  int64_t lda, n, row_begin, row_end;  // global rows [row_begin, row_end); A row 0 = row_begin
+  int64_t d;
+  int32_t k, rule;
+  uint64_t seed;
+  float scale;
+  int64_t R;        // chunk rows
+  int32_t NC;       // columns per work item (4, 8, 16, 32)
+  int32_t kb;       // blocks per block group
+  int32_t threads;  // threads per CTA
+  int32_t grid;     // CTAs (0 = automatic)
+};
+
+// Shared-memory bytes the tile kernel needs for (B, kb, NC, threads).
+size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads);
+int32_t tile_slots(int32_t NC, int32_t kb);
+// Enqueue the chunked tile kernel (atomic flush). Returns a CUDA error code.
+cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches);
+
+struct LiteralLaunch {
+  const float* A;
+  void* Y;
+  int64_t lda, n, row_begin, row_end, d;
+  int32_t k, rule;
+  uint64_t seed;
+  float scale;
+};
+cudaError_t launch_literal(const LiteralLaunch& L, cudaStream_t st, int32_t* launches);
+
+struct DetLaunch {
+  const float* A;
+  void* Y;
+  float* P;  // d x n FP32 scratch, zeroed by the launcher
+  int64_t lda, n, row_begin, row_end, d;
+  int32_t k, rule;
+  uint64_t seed;
+  float scale;
+  int64_t R;
+};
+cudaError_t launch_det(const DetLaunch& L, cudaStream_t st, int32_t* launches);
+
+cudaError_t launch_pattern(int64_t d, int32_t k, uint64_t seed, int64_t i0, int64_t cnt, int32_t* rows,
+                           int8_t* signs, cudaStream_t st);
+
+// FP64 sketch-and-solve back end: QR of [SA | Sb] (d x (n+1)), x = R^-1 (Q^T Sb)[:n].
+struct SolveLaunch {
+  const void* SA;   // d x n, float or binary16 (rule)
+  const void* Sb;   // d, same type
+  int32_t rule;
+  int64_t d, n;
+  double* part;     // scratch: partial sums, (ncta) * (n + 2) doubles
+  double* R;        // scratch: n x (n+1) doubles (R and Q^T Sb)
+  double* bcast;    // scratch: n doubles
+  unsigned* bar;    // scratch: 2 words, zero on entry
+  unsigned* status; // sticky status word
+  double* kappa;    // out: max|R_ii| / min|R_ii|
+  float* x;         // out: n floats
+  int32_t ncta;
+};
+// CTAs and rows per CTA the QR kernel will use for (d, n); 0 CTAs if unsupported.
+int32_t solve_ctas(int64_t d, int64_t n, int32_t sms, size_t smem_optin);
+cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launches);
+
+// Batched persistent kernel.
+struct BatchDesc;     // device-side item descriptor (sk_batch.cu)
+struct BatchWork;     // device-side work item
+cudaError_t launch_batch(const void* descs, const void* work, int64_t nwork, int32_t* counter, const void* zero_list,
+                         int32_t nzero, int32_t rule, int32_t threads, size_t smem, int32_t grid, cudaStream_t st,
+                         int32_t* launches);
+
+}  // namespace sk

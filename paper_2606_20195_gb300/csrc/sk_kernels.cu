@@ -1,0 +1,276 @@
+// Single-matrix sketch kernels: the chunked tile kernel (fast path), the paper-literal per-element
+// kernel (comparator), the canonical-order deterministic kernel (verification), and the S pattern
+// kernel. Paper Sec. 4.1 (SparseStack scatter) and Sec. 4.2 (FP16 variants).
+#include <algorithm>
+
+#include "sk_device.cuh"
+#include "sk_internal.h"
+#include "sk_tile.cuh"
+
+namespace sk {
+
+// ------------------------------------------------------------------ tile kernel
+struct TileGrid {
+  TileDesc D;
+  int64_t row_begin, row_end;  // global rows processed
+  int64_t R;                   // chunk rows
+  int64_t t_first;             // first chunk index
+  int64_t items;               // chunks * nbg * ncg
+  int32_t ncg, nbg;
+  int32_t acc_floats;          // floats of the accumulator (multiple of 4)
+};
+
+template <int RULE>
+__global__ void __launch_bounds__(1024) tile_kernel(const TileGrid P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* acc = reinterpret_cast<float*>(smem_raw);
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  uint64_t* hbuf = reinterpret_cast<uint64_t*>(smem_raw + (size_t)P.acc_floats * 4) + warp * 32;
+  for (int x = threadIdx.x; x < P.acc_floats; x += blockDim.x) acc[x] = 0.f;
+  __syncthreads();
+  const TileDesc& D = P.D;
+  for (int64_t w = blockIdx.x; w < P.items; w += gridDim.x) {
+    const int32_t g = (int32_t)(w % P.ncg);
+    const int64_t rest = w / P.ncg;
+    const int32_t bg = (int32_t)(rest % P.nbg);
+    const int64_t t = P.t_first + rest / P.nbg;
+    const int64_t r0 = max(t * P.R, P.row_begin);
+    const int64_t r1 = min((t + 1) * P.R, P.row_end);
+    const int32_t j0 = bg * D.kb;
+    const int32_t kbe = min(D.kb, (int32_t)D.k - j0);
+    tile_scatter(D, r0, r1, g, j0, kbe, acc, hbuf, warp, nwarps);
+    __syncthreads();
+    tile_flush<RULE>(D, t, g, j0, kbe, acc);
+    __threadfence();
+    __syncthreads();
+  }
+}
+
+int32_t tile_slots(int32_t NC, int32_t kb) { return std::min(32 / NC, kb); }
+
+size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads) {
+  const int32_t S = tile_slots(NC, kb);
+  const int64_t fl = tile_acc_floats((uint32_t)B, kb, S, NC);
+  return (size_t)fl * 4 + (size_t)(threads / 32) * 32 * 8;
+}
+
+static int ilog2(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches) {
+  TileGrid P;
+  const int64_t B = L.d / L.k;
+  P.D.A = L.A;
+  P.D.Y = L.Y;
+  P.D.lda = L.lda;
+  P.D.n = L.n;
+  P.D.row_base = L.row_begin;
+  P.D.seed = L.seed;
+  P.D.scale = L.scale;
+  P.D.B = (uint32_t)B;
+  P.D.k = (uint32_t)L.k;
+  P.D.kp = (uint32_t)((L.k + 1) / 2);
+  P.D.log2NC = ilog2(L.NC);
+  P.D.S = tile_slots(L.NC, L.kb);
+  P.D.kb = L.kb;
+  P.row_begin = L.row_begin;
+  P.row_end = L.row_end;
+  P.R = L.R;
+  P.t_first = L.row_begin / L.R;
+  const int64_t t_last = (L.row_end - 1) / L.R;
+  P.ncg = (int32_t)((L.n + L.NC - 1) / L.NC);
+  P.nbg = (L.k + L.kb - 1) / L.kb;
+  P.items = (t_last - P.t_first + 1) * P.ncg * P.nbg;
+  P.acc_floats = (int32_t)tile_acc_floats((uint32_t)B, L.kb, P.D.S, L.NC);
+  const size_t smem = tile_smem_bytes(B, L.kb, L.NC, L.threads);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  void (*kern)(const TileGrid);
+  switch (L.rule) {
+    case kRN: kern = tile_kernel<kRN>; break;
+    case kSR: kern = tile_kernel<kSR>; break;
+    case kDither: kern = tile_kernel<kDither>; break;
+    default: kern = tile_kernel<kFP32>; break;
+  }
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L.threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = L.grid > 0 ? L.grid : (int64_t)sms * per_sm;
+  grid = std::min<int64_t>(grid, P.items);
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, L.threads, smem, st>>>(P);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ paper-literal kernel
+// One thread per (input row, column pair): for each of the k nonzeros of the row's column of S,
+// scale, quantize (FP16 rules) and add with one atomic per element (FP32) or one packed half2
+// atomic per column pair (paper Listings 1 and 2). Equivalent to chunk length R = 1; the rounding
+// bits of contribution i use chunk index t = i.
+template <int RULE>
+__global__ void literal_kernel(const LiteralLaunch L, uint32_t B, uint32_t kp) {
+  const int64_t n = L.n;
+  const int64_t ncp = (n + 1) >> 1;
+  const int64_t total = (L.row_end - L.row_begin) * ncp;
+  const bool even = (n & 1) == 0;
+  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < total;
+       tid += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t il = tid / ncp;
+    const int64_t c0 = 2 * (tid - il * ncp);
+    const int64_t i = L.row_begin + il;
+    const bool has1 = c0 + 1 < n;
+    const float a0 = __ldg(L.A + il * L.lda + c0);
+    const float a1 = has1 ? __ldg(L.A + il * L.lda + c0 + 1) : 0.f;
+    uint64_t bits = 0;
+    for (uint32_t j = 0; j < (uint32_t)L.k; ++j) {
+      if ((j & 1u) == 0) bits = row_pair_bits(L.seed, (uint64_t)i, kp, j >> 1);
+      const uint32_t w = block_word(bits, j);
+      const uint32_t r = j * B + word_to_slot(w, B);
+      const bool neg = (w & 1u) != 0;
+      const float x0 = __fmul_rn(L.scale, neg ? -a0 : a0);
+      const float x1 = __fmul_rn(L.scale, neg ? -a1 : a1);
+      if (RULE == kFP32) {
+        float* y = reinterpret_cast<float*>(L.Y) + (int64_t)r * n + c0;
+        atomicAdd(y, x0);
+        if (has1) atomicAdd(y + 1, x1);
+      } else {
+        float u[4] = {0.f, 0.f, 0.f, 0.f};
+        if (RULE != kRN) uniforms4(L.seed, r, (uint32_t)(c0 >> 2), (uint64_t)i, u);
+        const __half q0 = quantize<RULE>(x0, u[c0 & 3]);
+        __half* y = reinterpret_cast<__half*>(L.Y) + (int64_t)r * n + c0;
+        if (has1) {
+          const __half q1 = quantize<RULE>(x1, u[(c0 + 1) & 3]);
+          if (even) {
+            atomicAdd(reinterpret_cast<__half2*>(y), __halves2half2(q0, q1));
+          } else {
+            atomicAdd(y, q0);
+            atomicAdd(y + 1, q1);
+          }
+        } else {
+          atomicAdd(y, q0);
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_literal(const LiteralLaunch& L, cudaStream_t st, int32_t* launches) {
+  const uint32_t B = (uint32_t)(L.d / L.k);
+  const uint32_t kp = (uint32_t)((L.k + 1) / 2);
+  const int64_t total = (L.row_end - L.row_begin) * ((L.n + 1) / 2);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256;
+  int64_t grid = std::min<int64_t>((total + threads - 1) / threads, (int64_t)sms * 8);
+  if (grid < 1) grid = 1;
+  switch (L.rule) {
+    case kRN: literal_kernel<kRN><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
+    case kSR: literal_kernel<kSR><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
+    case kDither: literal_kernel<kDither><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
+    default: literal_kernel<kFP32><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
+  }
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ deterministic kernel
+// Canonical order, bit for bit: one thread owns (block j, column c), i.e. outputs (jB..jB+B-1, c).
+// For every chunk it sums sign * A[i, c] over ascending rows into the FP32 partials P[s, c]
+// (from +0), then walks the chunk's rows again: at the first visit of a target the chunk total is
+// scaled, quantized and added into Y in FP32 or binary16 (round to nearest even), and the partial
+// is reset to +0; later visits of the same target add a quantized +0, which leaves Y unchanged.
+template <int RULE>
+__global__ void det_kernel(const DetLaunch L, uint32_t B, uint32_t kp) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = L.n;
+  if (tid >= (int64_t)L.k * n) return;
+  const uint32_t j = (uint32_t)(tid / n);
+  const int64_t c = tid - (int64_t)j * n;
+  const int64_t t0 = L.row_begin / L.R;
+  const int64_t t1 = (L.row_end - 1) / L.R;
+  for (int64_t t = t0; t <= t1; ++t) {
+    const int64_t r0 = max(t * L.R, L.row_begin);
+    const int64_t r1 = min((t + 1) * L.R, L.row_end);
+    for (int64_t i = r0; i < r1; ++i) {
+      const uint32_t w = block_word(row_pair_bits(L.seed, (uint64_t)i, kp, j >> 1), j);
+      const int64_t r = (int64_t)j * B + word_to_slot(w, B);
+      const float a = L.A[(i - L.row_begin) * L.lda + c];
+      float* p = L.P + r * n + c;
+      *p = __fadd_rn(*p, (w & 1u) ? -a : a);
+    }
+    for (int64_t i = r0; i < r1; ++i) {
+      const uint32_t w = block_word(row_pair_bits(L.seed, (uint64_t)i, kp, j >> 1), j);
+      const int64_t r = (int64_t)j * B + word_to_slot(w, B);
+      float* p = L.P + r * n + c;
+      const float x = __fmul_rn(L.scale, *p);
+      *p = 0.f;
+      if (RULE == kFP32) {
+        float* y = reinterpret_cast<float*>(L.Y) + r * n + c;
+        *y = __fadd_rn(*y, x);
+      } else {
+        float u[4] = {0.f, 0.f, 0.f, 0.f};
+        if (RULE != kRN) uniforms4(L.seed, (uint32_t)r, (uint32_t)(c >> 2), (uint64_t)t, u);
+        __half* y = reinterpret_cast<__half*>(L.Y) + r * n + c;
+        *y = __hadd(*y, quantize<RULE>(x, u[c & 3]));
+      }
+    }
+  }
+}
+
+cudaError_t launch_det(const DetLaunch& L, cudaStream_t st, int32_t* launches) {
+  const uint32_t B = (uint32_t)(L.d / L.k);
+  const uint32_t kp = (uint32_t)((L.k + 1) / 2);
+  cudaError_t e = cudaMemsetAsync(L.P, 0, sizeof(float) * (size_t)(L.d * L.n), st);
+  if (e != cudaSuccess) return e;
+  const int64_t total = (int64_t)L.k * L.n;
+  const int threads = 128;
+  const int64_t grid = (total + threads - 1) / threads;
+  switch (L.rule) {
+    case kRN: det_kernel<kRN><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
+    case kSR: det_kernel<kSR><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
+    case kDither: det_kernel<kDither><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
+    default: det_kernel<kFP32><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
+  }
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ S pattern
+__global__ void pattern_kernel(int64_t d, int32_t k, uint64_t seed, int64_t i0, int64_t cnt, int32_t* rows,
+                               int8_t* signs) {
+  const uint32_t B = (uint32_t)(d / k);
+  const uint32_t kp = (uint32_t)((k + 1) / 2);
+  const int64_t total = cnt * k;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = x / k;
+    const uint32_t j = (uint32_t)(x - q * k);
+    const uint32_t w = block_word(row_pair_bits(seed, (uint64_t)(i0 + q), kp, j >> 1), j);
+    rows[x] = (int32_t)(j * B + word_to_slot(w, B));
+    signs[x] = (w & 1u) ? (int8_t)-1 : (int8_t)1;
+  }
+}
+
+cudaError_t launch_pattern(int64_t d, int32_t k, uint64_t seed, int64_t i0, int64_t cnt, int32_t* rows,
+                           int8_t* signs, cudaStream_t st) {
+  const int64_t total = cnt * k;
+  const int threads = 256;
+  int64_t grid = std::min<int64_t>((total + threads - 1) / threads, 65535);
+  if (grid < 1) grid = 1;
+  pattern_kernel<<<(unsigned)grid, threads, 0, st>>>(d, k, seed, i0, cnt, rows, signs);
+  return cudaGetLastError();
+}
+
+}  // namespace sk

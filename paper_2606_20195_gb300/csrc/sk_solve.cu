@@ -1,0 +1,244 @@
+// FP64 back end of sketch-and-solve least squares (paper Sec. 5.1: minimize ||SA x - Sb||_2 through
+// a reduced QR of SA and a triangular solve). The paper factors in FP32; here the factorization,
+// Q^T Sb and the back substitution run in FP64.
+//
+// One cooperative launch factors W = [SA | Sb] (d x (n+1)) by Householder reflections. The d rows
+// are split across the CTAs (one per SM at most); each CTA keeps its rows of W in shared memory
+// for the whole factorization. Column step j needs two grid-wide reductions (the norm of column j
+// below the diagonal, then v^T W[:, c] for the trailing columns), done with FP64 atomics into
+// per-step buffers and separated by grid barriers. Row j of R is final after step j and is written
+// to global memory by its owner; CTA 0 finishes with the back substitution R x = (Q^T Sb)[:n].
+//
+// Every grid barrier spins with an iteration limit: on expiry the kernel sets kStatusTimeout in
+// the status word and all CTAs leave at the next check, so a stalled launch cannot hang the GPU.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "sk_device.cuh"
+#include "sk_internal.h"
+
+namespace sk {
+
+namespace {
+
+constexpr long long kSpinLimit = 1ll << 24;  // iterations of ~100 ns sleeps (~2 s)
+
+// Grid barrier for a co-resident (cooperative) grid. bar[0]: arrivals, bar[1]: generation.
+// Returns false if this CTA, or any CTA before it, gave up waiting.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g0) {
+        if (++spins > kSpinLimit) {
+          atomicOr(status, kStatusTimeout);
+          break;
+        }
+        // Another CTA already gave up: stop waiting.
+        if ((spins & 1023) == 0 && (*(volatile unsigned*)status & kStatusTimeout)) break;
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    ok = (*(volatile unsigned*)status & kStatusTimeout) == 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread receives the result.
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+struct QRArgs {
+  SolveLaunch L;
+  int32_t rpc;     // rows per CTA
+  double* nrm;     // n doubles, zeroed
+  double* wv;      // n * (n+1) doubles, zeroed
+};
+
+template <typename T>
+__device__ __forceinline__ double load_val(const void* p, int64_t idx) {
+  if constexpr (sizeof(T) == 2) return (double)__half2float(reinterpret_cast<const __half*>(p)[idx]);
+  else return (double)reinterpret_cast<const float*>(p)[idx];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
+  extern __shared__ __align__(16) double Wl[];  // rpc x (n+1), row-major
+  __shared__ double red[32];
+  __shared__ double sc[4];
+  const SolveLaunch& L = a.L;
+  const int64_t n = L.n, d = L.d, ldw = n + 1;
+  const int b = blockIdx.x;
+  const unsigned nb = gridDim.x;
+  const int64_t row0 = (int64_t)b * a.rpc;
+  const int64_t nown = max((int64_t)0, min((int64_t)a.rpc, d - row0));
+  // Load own rows of [SA | Sb] as FP64.
+  for (int64_t e = threadIdx.x; e < nown * ldw; e += blockDim.x) {
+    const int64_t rl = e / ldw, c = e - rl * ldw;
+    const int64_t r = row0 + rl;
+    Wl[e] = (c < n) ? load_val<T>(L.SA, r * n + c) : load_val<T>(L.Sb, r);
+  }
+  __syncthreads();
+  for (int64_t j = 0; j < n; ++j) {
+    // Phase A: squared norm of column j over rows >= j; owner of row j publishes W[j][j].
+    double ss = 0.0;
+    for (int64_t rl = threadIdx.x; rl < nown; rl += blockDim.x) {
+      if (row0 + rl >= j) {
+        const double v = Wl[rl * ldw + j];
+        ss += v * v;
+      }
+    }
+    ss = block_sum(ss, red);
+    if (threadIdx.x == 0) {
+      if (ss != 0.0) atomicAdd(&a.nrm[j], ss);
+      if (j >= row0 && j < row0 + nown) L.bcast[j] = Wl[(j - row0) * ldw + j];
+    }
+    if (!grid_barrier(L.bar, nb, L.status)) return;
+    // Phase B: reflector v = x - alpha e_j (alpha = -sign(x0) ||x||), partial v^T W[:, c].
+    if (threadIdx.x == 0) {
+      const double norm2 = __ldcg(&a.nrm[j]);
+      const double x0 = __ldcg(&L.bcast[j]);
+      const double alpha = -copysign(sqrt(norm2), x0);
+      const double vj = x0 - alpha;
+      const double vtv = (norm2 - x0 * x0) + vj * vj;
+      sc[0] = alpha;
+      sc[1] = vj;
+      sc[2] = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+    }
+    __syncthreads();
+    const double alpha = sc[0], vj = sc[1], tau = sc[2];
+    if (tau != 0.0) {
+      for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x) {
+        double dot = 0.0;
+        for (int64_t rl = 0; rl < nown; ++rl) {
+          const int64_t r = row0 + rl;
+          if (r < j) continue;
+          const double vr = (r == j) ? vj : Wl[rl * ldw + j];
+          dot += vr * Wl[rl * ldw + c];
+        }
+        if (dot != 0.0) atomicAdd(&a.wv[j * ldw + c], dot);
+      }
+    }
+    if (!grid_barrier(L.bar, nb, L.status)) return;
+    // Phase C: W[r][c] -= tau * v_r * w_c on own rows r >= j, columns c > j.
+    if (tau != 0.0) {
+      const int64_t ncols = n - j;  // columns j+1 .. n
+      for (int64_t e = threadIdx.x; e < nown * ncols; e += blockDim.x) {
+        const int64_t rl = e / ncols, c = j + 1 + (e - rl * ncols);
+        const int64_t r = row0 + rl;
+        if (r < j) continue;
+        const double vr = (r == j) ? vj : Wl[rl * ldw + j];
+        Wl[rl * ldw + c] -= tau * vr * __ldcg(&a.wv[j * ldw + c]);
+      }
+    }
+    __syncthreads();
+    if (j >= row0 && j < row0 + nown) {
+      const int64_t rl = j - row0;
+      if (threadIdx.x == 0) {
+        Wl[rl * ldw + j] = alpha;
+        L.R[j * ldw + j] = alpha;
+      }
+      for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x) L.R[j * ldw + c] = Wl[rl * ldw + c];
+    }
+    __syncthreads();
+  }
+  if (!grid_barrier(L.bar, nb, L.status)) return;
+  if (b != 0) return;
+  // Back substitution on CTA 0 (column-oriented): rhs in shared memory (reuses Wl).
+  double* rhs = Wl;
+  for (int64_t l = threadIdx.x; l < n; l += blockDim.x) rhs[l] = __ldcg(&L.R[l * ldw + n]);
+  __syncthreads();
+  double rmax = 0.0, rmin = 0.0;
+  bool singular = false;
+  for (int64_t j = n - 1; j >= 0; --j) {
+    const double rjj = __ldcg(&L.R[j * ldw + j]);
+    if (threadIdx.x == 0) {
+      const double xj = (rjj != 0.0) ? rhs[j] / rjj : 0.0;
+      rhs[j] = xj;
+      sc[3] = xj;
+    }
+    if (rjj == 0.0) singular = true;
+    const double arj = fabs(rjj);
+    if (j == n - 1) {
+      rmax = arj;
+      rmin = arj;
+    } else {
+      rmax = fmax(rmax, arj);
+      rmin = fmin(rmin, arj);
+    }
+    __syncthreads();
+    const double xj = sc[3];
+    for (int64_t l = threadIdx.x; l < j; l += blockDim.x) rhs[l] -= __ldcg(&L.R[l * ldw + j]) * xj;
+    __syncthreads();
+  }
+  for (int64_t l = threadIdx.x; l < n; l += blockDim.x) L.x[l] = singular ? __int_as_float(0x7fc00000) : (float)rhs[l];
+  if (threadIdx.x == 0) {
+    if (singular) atomicOr(L.status, kStatusNumeric);
+    *L.kappa = (rmin > 0.0) ? rmax / rmin : __longlong_as_double(0x7ff0000000000000ll);
+  }
+}
+
+}  // namespace
+
+int32_t solve_ctas(int64_t d, int64_t n, int32_t sms, size_t smem_optin) {
+  if (n < 1 || d < n) return 0;
+  const size_t budget = smem_optin > 4096 ? smem_optin - 4096 : 0;
+  int64_t ncta = std::min<int64_t>(sms, std::max<int64_t>(1, (d + 7) / 8));
+  for (; ncta <= sms; ++ncta) {
+    const int64_t rpc = (d + ncta - 1) / ncta;
+    if ((size_t)rpc * (size_t)(n + 1) * 8 <= budget) return (int32_t)ncta;
+  }
+  return 0;
+}
+
+cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launches) {
+  QRArgs a;
+  a.L = L;
+  a.rpc = (int32_t)((L.d + L.ncta - 1) / L.ncta);
+  // part scratch holds nrm (n) followed by wv (n * (n+1)).
+  a.nrm = L.part;
+  a.wv = L.part + L.n;
+  cudaError_t e = cudaMemsetAsync(L.part, 0, sizeof(double) * (size_t)(L.n + L.n * (L.n + 1)), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(L.bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const size_t smem = std::max<size_t>((size_t)a.rpc * (size_t)(L.n + 1) * 8, (size_t)L.n * 8);
+  void* args[] = {(void*)&a};
+  const void* kern = (L.rule == kFP32) ? (const void*)qr64_kernel<float> : (const void*)qr64_kernel<__half>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)L.ncta), dim3(256), args, smem, st);
+  if (launches) *launches += 1;
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace sk

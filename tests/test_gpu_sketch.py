@@ -1,0 +1,180 @@
+"""GPU parity of the sketch kernels against the CPU oracle, through the C ABI (libsk.so).
+
+Bars (paper Sec. 4.1-4.2 semantics): the S pattern and the deterministic / serial-tile modes are
+bit-exact with the oracle's canonical order for every rule; the atomic (fast) mode matches the
+FP64 sketch within relative Frobenius error 1e-5 (FP32) and 2e-3 (FP16 rules).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_20195_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RULES = [0, 1, 2, 3]
+TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3}
+
+
+def _to_np(Y, rule):
+    Yc = Y.cpu().numpy()
+    return Yc if rule == 0 else Yc.view(np.uint16)
+
+
+def _as64(Yn, rule):
+    return Yn.astype(np.float64) if rule == 0 else oracle.halfbits_to_f64(Yn)
+
+
+def _apply(sk, A_h, d, k, rule, seed, dev, **params):
+    import torch
+    A = torch.from_numpy(np.ascontiguousarray(A_h)).to(dev)
+    plan = sk.Plan(d, A_h.shape[0], k, rule, seed, **params)
+    Y = plan.apply(A)
+    torch.cuda.synchronize()
+    out = _to_np(Y, rule)
+    launches = plan.get(sk.SK_PARAM_LAST_LAUNCHES)
+    R = plan.get(sk.SK_PARAM_LAST_CHUNK_ROWS)
+    plan.close()
+    return out, launches, R
+
+
+@pytest.mark.parametrize("d,k", [(256, 4), (256, 1), (4096, 8), (96, 3), (64, 64)])
+def test_pattern_bit_exact(sk, dev, d, k):
+    import torch
+    m, i0, seed = 20000, 123457, 0xDEADBEEF12345678
+    plan = sk.Plan(d, i0 + m, k, 0, seed)
+    rows = torch.empty(m * k, dtype=torch.int32, device=dev)
+    signs = torch.empty(m * k, dtype=torch.int8, device=dev)
+    sk.sk_materialize_S(plan.handle, i0, m, rows, signs)
+    torch.cuda.synchronize()
+    ref_r, ref_s = oracle.s_pattern(d, k, seed, m, i0=i0)
+    assert np.array_equal(rows.cpu().numpy().reshape(m, k), ref_r.astype(np.int32))
+    assert np.array_equal(signs.cpu().numpy().reshape(m, k), ref_s)
+    plan.close()
+
+
+@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("k", [4, 1])
+@pytest.mark.parametrize("R", [1, 256, 4096])
+def test_deterministic_mode_bit_exact(sk, dev, rule, k, R):
+    m, n, d, seed = 16384, 16, 256, 0
+    A = inputs.host_matrix(m, n, "incoherent", seed=0)
+    got, _, _ = _apply(sk, A, d, k, rule, seed, dev, mode=sk.SK_MODE_DETERMINISTIC, chunk_rows=R)
+    ref = oracle.sketch_canonical(A, d, k, seed, rule, R)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("k,cols", [(4, 8), (4, 16), (4, 32), (1, 32), (8, 4), (8, 8)])
+def test_serial_tile_bit_exact(sk, dev, rule, k, cols):
+    # The fast tile kernel run by one warp of one CTA follows the canonical order: bit-exact.
+    m, n, d, seed, R = 9000, 13, 256, 5, 1000
+    A = inputs.host_matrix(m, n, "incoherent", seed=1)
+    got, _, _ = _apply(sk, A, d, k, rule, seed, dev, mode=sk.SK_MODE_SERIAL_TILE, chunk_rows=R, tile_cols=cols)
+    ref = oracle.sketch_canonical(A, d, k, seed, rule, R)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("k", [4, 1])
+def test_atomic_mode_c0_tolerance(sk, dev, rule, k):
+    m, n, d, seed = 16384, 16, 256, 0
+    A = inputs.host_matrix(m, n, "incoherent", seed=0)
+    got, launches, R = _apply(sk, A, d, k, rule, seed, dev)
+    Y64 = oracle.sketch_f64(A, d, k, seed)
+    err = oracle.rel_fro(_as64(got, rule), Y64)
+    assert err <= TOL[rule], err
+    assert launches == 1
+    # the canonical result for the same chunking is within the same tolerance of the kernel
+    ref = _as64(oracle.sketch_canonical(A, d, k, seed, rule, R), rule)
+    assert oracle.rel_fro(_as64(got, rule), ref) <= TOL[rule]
+
+
+@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("shape", [(1, 1, 8, 1), (7, 3, 12, 3), (1000, 1, 64, 8), (4099, 33, 120, 4),
+                                   (50001, 5, 512, 2), (3, 2, 64, 64)])
+def test_atomic_mode_ragged_and_edges(sk, dev, rule, shape):
+    # Ragged row counts (not a multiple of any tile), odd and tiny n, d = k (B = 1 at k = 64 rows)
+    m, n, d, k = shape
+    A = inputs.host_matrix(m, n, "incoherent", seed=m)
+    got, _, _ = _apply(sk, A, d, k, rule, 77, dev)
+    Y64 = oracle.sketch_f64(A, d, k, 77)
+    assert oracle.rel_fro(_as64(got, rule), Y64) <= TOL[rule]
+
+
+@pytest.mark.parametrize("rule", RULES)
+def test_lda_and_row_offset(sk, dev, rule):
+    import torch
+    m, n, lda, d, k, off = 6000, 10, 24, 128, 4, 100003
+    full = inputs.host_matrix(m, lda, "incoherent", seed=3)
+    A = torch.from_numpy(full).to(dev)[:, :n]  # stride lda
+    plan = sk.Plan(d, m, k, rule, 9, row_offset=off)
+    Y = plan.apply(A)
+    torch.cuda.synchronize()
+    got = _as64(_to_np(Y, rule), rule)
+    # oracle: the same rows placed at global offset `off` (zeros before contribute nothing)
+    Af = np.zeros((off + m, n), dtype=np.float32)
+    Af[off:] = full[:, :n]
+    Y64 = oracle.sketch_f64(Af, d, k, 9)
+    assert oracle.rel_fro(got, Y64) <= TOL[rule]
+    plan.close()
+
+
+@pytest.mark.parametrize("rule", RULES)
+def test_literal_kernel(sk, dev, rule):
+    # The paper-literal kernel (R = 1, one atomic per element and nonzero) against the FP64
+    # sketch; FP16 rules at R = 1 are less accurate (T = k m / d contributions per output), so the
+    # bound here is the canonical R = 1 error plus the FP16 tolerance.
+    m, n, d, k, seed = 4096, 16, 256, 4, 3
+    A = inputs.host_matrix(m, n, "incoherent", seed=2)
+    got, _, R = _apply(sk, A, d, k, rule, seed, dev, kernel=sk.SK_KERNEL_LITERAL)
+    assert R == 1
+    Y64 = oracle.sketch_f64(A, d, k, seed)
+    canon = _as64(oracle.sketch_canonical(A, d, k, seed, rule, 1), rule)
+    e_canon = oracle.rel_fro(canon, Y64)
+    assert oracle.rel_fro(_as64(got, rule), Y64) <= e_canon + TOL[rule]
+    # with FP32 adds in a different order the two agree to FP32 precision
+    if rule == 0:
+        assert oracle.rel_fro(_as64(got, rule), canon) <= 1e-6
+
+
+def test_deterministic_matches_serial_and_is_repeatable(sk, dev):
+    m, n, d, k = 20000, 12, 256, 4
+    A = inputs.host_matrix(m, n, "coherent", seed=4)
+    for rule in RULES:
+        a, _, _ = _apply(sk, A, d, k, rule, 1, dev, mode=sk.SK_MODE_DETERMINISTIC, chunk_rows=2048)
+        b, _, _ = _apply(sk, A, d, k, rule, 1, dev, mode=sk.SK_MODE_SERIAL_TILE, chunk_rows=2048, tile_cols=16)
+        c, _, _ = _apply(sk, A, d, k, rule, 1, dev, mode=sk.SK_MODE_DETERMINISTIC, chunk_rows=2048)
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_invalid_arguments_are_rejected(sk, dev):
+    import torch
+    with pytest.raises(sk.SkError) as e:
+        sk.sk_plan_create(10, 100, 4, 0, 0)  # d % k != 0
+    assert e.value.status == sk.SK_ERR_INVALID_ARG
+    with pytest.raises(sk.SkError):
+        sk.sk_plan_create(64, 0, 4, 0, 0)
+    with pytest.raises(sk.SkError):
+        sk.sk_plan_create(64, 10, 0, 0, 0)
+    with pytest.raises(sk.SkError):
+        sk.sk_plan_create(64, 10, 4, 9, 0)
+    plan = sk.Plan(64, 100, 4, 0, 0)
+    A = torch.zeros((100, 8), device=dev)
+    Y = torch.zeros((64, 8), device=dev)
+    with pytest.raises(sk.SkError):
+        sk.sk_apply(plan.handle, A, 4, 8, Y)  # lda < n
+    with pytest.raises(sk.SkError):
+        sk.sk_apply(plan.handle, 0, 8, 8, Y)  # NULL A
+    with pytest.raises(sk.SkError):
+        sk.sk_plan_set(plan.handle, 99, 1)
+    with pytest.raises(sk.SkError):
+        sk.sk_plan_set(plan.handle, sk.SK_PARAM_TILE_COLS, 12)
+    with pytest.raises(sk.SkError):
+        sk.sk_plan_set(plan.handle, sk.SK_PARAM_KERNEL, sk.SK_KERNEL_LITERAL)
+        sk.sk_plan_set(plan.handle, sk.SK_PARAM_CHUNK_ROWS, 8)
+        sk.sk_apply(plan.handle, A, 8, 8, Y)
+    assert "literal" in sk.sk_last_error()
+    plan.close()
+    # nothing was enqueued by the rejected calls: the context is healthy
+    torch.cuda.synchronize()
