@@ -35,6 +35,8 @@ WORKLOADS = {
     # name: (m, n, d, k)
     "sweep_m4M_n64_d4096_k8": (1 << 22, 64, 4096, 8),
     "small_m16384_n16_d256_k4": (16384, 16, 256, 4),
+    # same kernel shape at a quarter of the rows: the ncu capture case (256 MiB of A, > L2)
+    "profile_m1M_n64_d4096_k8": (1 << 20, 64, 4096, 8),
 }
 DEFAULT_WORKLOAD = "sweep_m4M_n64_d4096_k8"
 METRIC = "SA sketch HBM GB/s (% of peak) FP16 vs FP32 at equal distortion; p99 solve ms"

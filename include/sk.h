@@ -82,7 +82,10 @@ typedef enum {
   /* Read-only: number of kernel launches the last sk_apply/sk_solve enqueued. */
   SK_PARAM_LAST_LAUNCHES = 7,
   /* Read-only: the chunk length R the last sk_apply used. */
-  SK_PARAM_LAST_CHUNK_ROWS = 8
+  SK_PARAM_LAST_CHUNK_ROWS = 8,
+  /* Read-only: sticky status bits the sketch kernels of this plan set on the device (bit 0: a
+   * bounded wait gave up, the results of that call are invalid). Reading it synchronizes the device. */
+  SK_PARAM_DEVICE_STATUS = 9
 } sk_param;
 
 enum { SK_MODE_ATOMIC = 0, SK_MODE_DETERMINISTIC = 1, SK_MODE_SERIAL_TILE = 2 };

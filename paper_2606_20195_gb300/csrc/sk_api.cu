@@ -52,6 +52,11 @@ struct sk_plan_s {
   // device scratch
   float* det_P = nullptr;
   size_t det_P_bytes = 0;
+  unsigned* dstatus = nullptr;  // sticky device status word of the sketch kernels
+  float* tileP = nullptr;       // two-level chunk totals (zero between launches)
+  size_t tileP_bytes = 0;
+  int32_t* counters = nullptr;  // slice counters (zero between launches)
+  size_t counters_bytes = 0;
   void* solve_buf = nullptr;
   size_t solve_bytes = 0;
   size_t solve_status_off = 0, solve_kappa_off = 0;
@@ -92,26 +97,37 @@ size_t elem_size(int32_t rule) { return rule == SK_FP32 ? 4 : 2; }
 
 // Tile-kernel configuration for a plan and a column count.
 struct TileCfg {
-  int32_t NC = 0, kb = 0, threads = 0, grid = 0;
+  int32_t NC = 0, kb = 0, threads = 0, grid = 0, slices = 1, depth = 1;
   int64_t R = 0;
   bool serial = false;
 };
 
+// Default chunk length: at most 8 chunks per matrix (each output then receives at most 8 rounded
+// contributions) and at least 4096 rows per chunk; a multiple of 32.
+int64_t default_chunk_rows(int64_t m) {
+  int64_t R = std::max<int64_t>(4096, (m + 7) / 8);
+  return ((R + 31) / 32) * 32;
+}
+
 sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, TileCfg* cfg) {
   const bool serial = (p->mode == SK_MODE_SERIAL_TILE);
   const int32_t threads = serial ? 32 : (p->threads > 0 ? p->threads : 1024);
-  const size_t hbytes = (size_t)(threads / 32) * 32 * 8;
-  const size_t optin = (size_t)std::min(di.optin, 232448);
-  if (optin <= hbytes + 1024) return set_error(SK_ERR_UNSUPPORTED, "shared memory too small");
-  const size_t budget_floats = (optin - hbytes - 1024) / 4;
+  const int32_t nwarps = threads / 32;
+  const int32_t RB = 32 / ((p->k + 1) / 2);
+  const size_t optin = (size_t)std::min(di.optin, 232448) - 1024;
+  // Fits: accumulator + target words + a ring of at least one slot per warp.
+  auto fits = [&](int32_t c, int32_t kbt) {
+    const int64_t fl = tile_acc_floats((uint32_t)p->B, kbt, tile_slots(c, kbt), c);
+    return tile_smem_bytes(p->B, kbt, c, threads, p->k, 1) <= optin && fl < (1 << 29);
+  };
   const int32_t widths[4] = {32, 16, 8, 4};
   int32_t NC = 0, kb = 0;
   for (int32_t c : widths) {
     if (p->tile_cols > 0 && c != p->tile_cols) continue;
-    if (!serial && c > 4 && c / 2 >= n) continue;
+    if (!serial && c > 4 && (c / 2 >= n || c * RB > 256)) continue;
     // Serial (verification) mode needs the lane groups of a pass to hit distinct blocks.
     if (serial && (32 / c > p->k || p->k % (32 / c) != 0)) continue;
-    if ((size_t)tile_acc_floats((uint32_t)p->B, p->k, tile_slots(c, p->k), c) <= budget_floats) {
+    if (fits(c, p->k)) {
       NC = c;
       kb = p->k;
       break;
@@ -120,7 +136,7 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
   if (NC == 0 && !serial) {
     NC = p->tile_cols > 0 ? p->tile_cols : 4;
     for (int32_t kbt = p->k; kbt >= 1; --kbt) {
-      if ((size_t)tile_acc_floats((uint32_t)p->B, kbt, tile_slots(NC, kbt), NC) <= budget_floats) {
+      if (fits(NC, kbt)) {
         kb = kbt;
         break;
       }
@@ -130,23 +146,30 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
     return set_error(SK_ERR_UNSUPPORTED,
                      "tile kernel: a block of %lld rows does not fit in shared memory with the requested width",
                      (long long)p->B);
-  const int64_t ncg = (n + NC - 1) / NC;
-  const int64_t nbg = (p->k + kb - 1) / kb;
-  int64_t R = p->R;
-  if (R <= 0) {
-    // One wave of work items over the SMs, at most 32 chunks per output (each output then receives
-    // at most 32 rounded contributions), chunk rows a multiple of 32.
-    const int64_t slots = (int64_t)di.sms;
-    int64_t chunks = (slots + ncg * nbg - 1) / (ncg * nbg);
-    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, 32));
-    R = (rows + chunks - 1) / chunks;
-    R = std::max<int64_t>(32, ((R + 31) / 32) * 32);
+  int32_t depth = 1;
+  while (depth < kMaxRingDepth && tile_smem_bytes(p->B, kb, NC, threads, p->k, depth + 1) <= optin) ++depth;
+  int64_t R = p->R > 0 ? p->R : default_chunk_rows(p->m);
+  int32_t slices = 1;
+  if (!serial) {
+    // Split chunks into slices until there are ~4 work items per resident CTA, keeping slices at
+    // least max(4096, 2d) rows long so the partial flush (d x NC floats) stays small.
+    const int64_t ncg = (n + NC - 1) / NC;
+    const int64_t nbg = (p->k + kb - 1) / kb;
+    const int64_t chunks = (rows + R - 1) / R + 1;
+    const int32_t cps = tile_ctas_per_sm(p->rule, threads, tile_smem_bytes(p->B, kb, NC, threads, p->k, depth));
+    const int64_t target = 4 * (int64_t)di.sms * std::max(cps, 1);
+    const int64_t per_chunk = std::max<int64_t>(1, (target + chunks * ncg * nbg - 1) / (chunks * ncg * nbg));
+    const int64_t min_rows = std::max<int64_t>(4096, 2 * p->d);
+    const int64_t max_slices = std::max<int64_t>(1, std::min(R, rows) / min_rows);
+    slices = (int32_t)std::min<int64_t>(per_chunk, std::min<int64_t>(max_slices, 4096));
   }
   cfg->NC = NC;
   cfg->kb = kb;
   cfg->threads = threads;
   cfg->grid = serial ? 1 : 0;
   cfg->R = R;
+  cfg->slices = slices;
+  cfg->depth = depth;
   cfg->serial = serial;
   return SK_OK;
 }
@@ -167,7 +190,7 @@ sk_status validate_apply(const sk_plan_s* p, const void* A, int64_t lda, int64_t
 // Enqueue Y = S * A for rows [row_begin, row_begin + rows) (A row 0 = row_begin) with chunk rows R.
 // Y must already be zero.
 sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, int64_t row_begin, int64_t rows, void* Y,
-                         int64_t R_fixed, cudaStream_t st, int32_t* launches, int64_t* R_used) {
+                         int64_t R_fixed, cudaStream_t st, int32_t* launches, int64_t* R_used, int64_t col_off = 0) {
   DevInfo di;
   sk_status s = dev_info(&di);
   if (s != SK_OK) return s;
@@ -206,6 +229,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
     L.seed = p->seed;
     L.scale = p->scale;
     L.R = R;
+    L.col_off = col_off;
     cudaError_t e = launch_det(L, st, launches);
     if (e != cudaSuccess) return cuda_fail(e, "deterministic kernel launch");
     if (R_used) *R_used = R;
@@ -225,13 +249,14 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
     L.rule = p->rule;
     L.seed = p->seed;
     L.scale = p->scale;
+    L.col_off = col_off;
     cudaError_t e = launch_literal(L, st, launches);
     if (e != cudaSuccess) return cuda_fail(e, "literal kernel launch");
     if (R_used) *R_used = 1;
     return SK_OK;
   }
   TileCfg cfg;
-  s = choose_tile(p, n, p->m, di, &cfg);
+  s = choose_tile(p, n, rows, di, &cfg);
   if (s != SK_OK) return s;
   if (R_fixed > 0) cfg.R = R_fixed;
   TileLaunch L;
@@ -251,6 +276,54 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
   L.kb = cfg.kb;
   L.threads = cfg.threads;
   L.grid = cfg.grid;
+  L.slices = cfg.slices;
+  L.depth = cfg.depth;
+  L.col_off = col_off;
+  L.allow_tma = 1;
+  if (!p->dstatus) {
+    if (cudaMalloc(&p->dstatus, sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(SK_ERR_OOM, "status word");
+    }
+    cudaError_t ez = cudaMemsetAsync(p->dstatus, 0, sizeof(unsigned), st);
+    if (ez != cudaSuccess) return cuda_fail(ez, "zeroing status word");
+  }
+  L.status = p->dstatus;
+  L.P = nullptr;
+  L.counters = nullptr;
+  if (cfg.slices > 1) {
+    int64_t chunks;
+    int32_t ncg, nbg;
+    tile_geometry(L, &chunks, &ncg, &nbg);
+    const size_t needP = sizeof(float) * (size_t)chunks * (size_t)(p->d * n);
+    const size_t needC = sizeof(int32_t) * (size_t)(chunks * ncg * nbg);
+    if (p->tileP_bytes < needP) {
+      if (p->tileP) cudaFree(p->tileP);
+      p->tileP = nullptr;
+      p->tileP_bytes = 0;
+      if (cudaMalloc(&p->tileP, needP) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SK_ERR_OOM, "chunk-total scratch (%zu bytes)", needP);
+      }
+      cudaError_t ez = cudaMemsetAsync(p->tileP, 0, needP, st);
+      if (ez != cudaSuccess) return cuda_fail(ez, "zeroing chunk totals");
+      p->tileP_bytes = needP;
+    }
+    if (p->counters_bytes < needC) {
+      if (p->counters) cudaFree(p->counters);
+      p->counters = nullptr;
+      p->counters_bytes = 0;
+      if (cudaMalloc(&p->counters, needC) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SK_ERR_OOM, "slice counters (%zu bytes)", needC);
+      }
+      cudaError_t ez = cudaMemsetAsync(p->counters, 0, needC, st);
+      if (ez != cudaSuccess) return cuda_fail(ez, "zeroing counters");
+      p->counters_bytes = needC;
+    }
+    L.P = p->tileP;
+    L.counters = p->counters;
+  }
   cudaError_t e = launch_tile(L, st, launches);
   if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");
   if (R_used) *R_used = cfg.R;
@@ -335,6 +408,17 @@ sk_status sk_plan_get(sk_plan p, int32_t key, int64_t* v) {
     case SK_PARAM_THREADS: *v = p->threads; return SK_OK;
     case SK_PARAM_LAST_LAUNCHES: *v = p->last_launches; return SK_OK;
     case SK_PARAM_LAST_CHUNK_ROWS: *v = p->last_R; return SK_OK;
+    case SK_PARAM_DEVICE_STATUS: {
+      *v = 0;
+      if (!p->dstatus) return SK_OK;
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return cuda_fail(e, "device status");
+      unsigned w = 0;
+      e = cudaMemcpy(&w, p->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "device status");
+      *v = (int64_t)w;
+      return SK_OK;
+    }
     default: return set_error(SK_ERR_INVALID_ARG, "unknown key %d", key);
   }
 }
@@ -533,7 +617,8 @@ sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const floa
   int64_t R_used = 0;
   s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, base + Lo.ya, 0, st, &launches, &R_used);
   if (s != SK_OK) return s;
-  s = enqueue_sketch(p, b, 1, 1, p->row_offset, p->m, base + Lo.yb, R_used, st, &launches, nullptr);
+  // Sb is column n of [A | b]: the same chunks, and the rounding bits of global column n.
+  s = enqueue_sketch(p, b, 1, 1, p->row_offset, p->m, base + Lo.yb, R_used, st, &launches, nullptr, n);
   if (s != SK_OK) return s;
   SolveLaunch L;
   L.SA = base + Lo.ya;
@@ -579,6 +664,9 @@ void sk_destroy(sk_plan p) {
   if (!p) return;
   cudaDeviceSynchronize();
   if (p->det_P) cudaFree(p->det_P);
+  if (p->dstatus) cudaFree(p->dstatus);
+  if (p->tileP) cudaFree(p->tileP);
+  if (p->counters) cudaFree(p->counters);
   if (p->solve_buf) cudaFree(p->solve_buf);
   for (int b = 0; b < 2; ++b) {
     if (p->stage[b]) cudaFree(p->stage[b]);

@@ -7,6 +7,8 @@
 // sk_batch_launch enqueues exactly two kernels (zero every Y_i and reset the counter; then the
 // persistent kernel), allocates nothing and never synchronizes, so it can be captured in a CUDA
 // graph and replayed.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -54,31 +56,35 @@ __global__ void batch_zero_kernel(const ZeroSpan* spans, int32_t nspan, int32_t*
 template <int RULE>
 __global__ void __launch_bounds__(1024) batch_kernel(const BatchDesc* __restrict__ descs,
                                                      const BatchWork* __restrict__ work, int64_t nwork,
-                                                     int32_t* counter) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                     int32_t* counter, int64_t acc_floats, int32_t slot_bytes,
+                                                     int32_t depth, unsigned* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int64_t next;
   __shared__ BatchDesc dsh;
+  __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   float* acc = reinterpret_cast<float*>(smem_raw);
-  // The accumulator takes the dynamic shared memory minus the per-warp stream buffers at its end.
-  uint32_t dyn = 0;
-  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-  const uint32_t hbytes = (uint32_t)nwarps * 32u * 8u;
-  uint64_t* hbuf = reinterpret_cast<uint64_t*>(smem_raw + (dyn - hbytes)) + warp * 32;
-  const int64_t acc_floats = (int64_t)(dyn - hbytes) / 4;
+  const SmemPlan SL = smem_plan(acc_floats, nwarps, slot_bytes, depth);
+  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem_raw + SL.wbuf_off) + warp * kWordsPerWarp;
+  WarpRing ring = make_ring(smem_raw, SL, warp);
   for (int64_t x = threadIdx.x; x < acc_floats; x += blockDim.x) acc[x] = 0.f;
+  if (threadIdx.x == 0) abort_flag = 0;
   __syncthreads();
   while (true) {
     if (threadIdx.x == 0) next = (int64_t)atomicAdd(counter, 1);
     __syncthreads();
     const int64_t w = next;
-    if (w >= nwork) break;
+    if (w >= nwork || abort_flag) break;
     const BatchWork wk = work[w];
     if (threadIdx.x == 0) dsh = descs[wk.item];
     __syncthreads();
-    tile_scatter(dsh.D, wk.r0, wk.r1, wk.g, wk.j0, wk.kbe, acc, hbuf, warp, nwarps);
+    if (!tile_scatter(dsh.D, wk.r0, wk.r1, wk.g, wk.j0, wk.kbe, acc, wbuf, ring, warp, nwarps)) {
+      abort_flag = 1;
+      if (status) atomicOr(status, kStatusTimeout);
+    }
     __syncthreads();
+    if (abort_flag) break;
     tile_flush<RULE>(dsh.D, wk.t, wk.g, wk.j0, wk.kbe, acc);
     __threadfence();
     __syncthreads();
@@ -86,8 +92,8 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchDesc* __restrict
 }
 
 cudaError_t launch_batch(const void* descs, const void* work, int64_t nwork, int32_t* counter, const void* zero_list,
-                         int32_t nzero, int32_t rule, int32_t threads, size_t smem, int32_t grid, cudaStream_t st,
-                         int32_t* launches) {
+                         int32_t nzero, int32_t rule, int32_t threads, size_t smem, int32_t grid, int64_t acc_floats,
+                         int32_t slot_bytes, int32_t depth, unsigned* status, cudaStream_t st, int32_t* launches) {
   dim3 zg(64, (unsigned)std::min(nzero, 1024));
   batch_zero_kernel<<<zg, 256, 0, st>>>(reinterpret_cast<const ZeroSpan*>(zero_list), nzero, counter);
   if (launches) *launches += 1;
@@ -96,10 +102,10 @@ cudaError_t launch_batch(const void* descs, const void* work, int64_t nwork, int
   const BatchDesc* dd = reinterpret_cast<const BatchDesc*>(descs);
   const BatchWork* ww = reinterpret_cast<const BatchWork*>(work);
   switch (rule) {
-    case kRN: batch_kernel<kRN><<<grid, threads, smem, st>>>(dd, ww, nwork, counter); break;
-    case kSR: batch_kernel<kSR><<<grid, threads, smem, st>>>(dd, ww, nwork, counter); break;
-    case kDither: batch_kernel<kDither><<<grid, threads, smem, st>>>(dd, ww, nwork, counter); break;
-    default: batch_kernel<kFP32><<<grid, threads, smem, st>>>(dd, ww, nwork, counter); break;
+    case kRN: batch_kernel<kRN><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
+    case kSR: batch_kernel<kSR><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
+    case kDither: batch_kernel<kDither><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
+    default: batch_kernel<kFP32><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
   }
   if (launches) *launches += 1;
   return cudaGetLastError();
@@ -126,6 +132,11 @@ struct sk_batch_s {
   bool built = false;
   int device = 0;
   // device state
+  CUtensorMap* d_maps = nullptr;
+  unsigned* d_status = nullptr;
+  int64_t acc_floats = 0;
+  int32_t slot_bytes = 0;
+  int32_t depth = 1;
   BatchDesc* d_descs = nullptr;
   BatchWork* d_work = nullptr;
   ZeroSpan* d_zero = nullptr;
@@ -139,6 +150,10 @@ struct sk_batch_s {
 namespace {
 
 void free_batch_dev(sk_batch_s* b) {
+  if (b->d_maps) cudaFree(b->d_maps);
+  if (b->d_status) cudaFree(b->d_status);
+  b->d_maps = nullptr;
+  b->d_status = nullptr;
   if (b->d_descs) cudaFree(b->d_descs);
   if (b->d_work) cudaFree(b->d_work);
   if (b->d_zero) cudaFree(b->d_zero);
@@ -157,24 +172,29 @@ sk_status build_batch(sk_batch_s* b) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   b->device = dev;
   const int32_t threads = b->threads > 0 ? b->threads : 1024;
-  const size_t hbytes = (size_t)(threads / 32) * 32 * 8;
-  const size_t budget = (size_t)std::min(optin, 232448) - hbytes - 1024;
-  const size_t budget_floats = budget / 4;
+  const int32_t nwarps = threads / 32;
+  // Ring slots hold at most 1 KiB (NC * RB * 4 bytes); two slots per warp are reserved when sizing
+  // the accumulators, and the ring gets deeper if the largest accumulator leaves room.
+  const size_t optin_c = (size_t)std::min(optin, 232448) - 1024;
+  const size_t fixed = (size_t)nwarps * (kWordsPerWarp * 4 + 2 * 1024 + 2 * 8) + 256;
+  const size_t budget_floats = (optin_c - fixed) / 4;
   const int32_t count = (int32_t)b->items.size();
   std::vector<BatchDesc> descs(count);
   std::vector<int32_t> ncgs(count), nbgs(count);
   size_t max_floats = 0;
+  int32_t slot_max = 128;
   double total_cost = 0.0;
   for (int32_t i = 0; i < count; ++i) {
     const sk_batch_item& it = b->items[i];
     const int64_t B = it.d / it.k;
-    // Widest column group (not wider than needed) whose accumulator holds all k blocks; if none
-    // does, the narrowest allowed width with as many blocks per group as fit.
+    const int32_t RB = 32 / ((it.k + 1) / 2);
+    // Widest column group (not wider than needed, slot at most 1 KiB) whose accumulator holds all
+    // k blocks; if none does, the narrowest width with as many blocks per group as fit.
     int32_t NC = 0, kb = 0;
     const int32_t widths[4] = {32, 16, 8, 4};
     for (int32_t c : widths) {
       if (b->tile_cols > 0 && c != b->tile_cols) continue;
-      if (c > 4 && c / 2 >= it.n) continue;
+      if (c > 4 && (c / 2 >= it.n || c * RB > 256)) continue;
       if ((size_t)tile_acc_floats((uint32_t)B, it.k, tile_slots(c, it.k), c) <= budget_floats) {
         NC = c;
         kb = it.k;
@@ -193,6 +213,7 @@ sk_status build_batch(sk_batch_s* b) {
     if (kb == 0)
       return set_error(SK_ERR_UNSUPPORTED, "batch item %d: a block of %lld rows does not fit in shared memory", i,
                        (long long)B);
+    slot_max = std::max(slot_max, ring_slot_bytes(RB, NC));
     BatchDesc& D = descs[i];
     D.D.A = it.A_dev;
     D.D.Y = it.Y_dev;
@@ -209,6 +230,8 @@ sk_status build_batch(sk_batch_s* b) {
     D.D.log2NC = l2;
     D.D.S = tile_slots(NC, kb);
     D.D.kb = kb;
+    D.D.col_off = 0;
+    D.D.tmap = nullptr;  // set after the maps are uploaded
     ncgs[i] = (int32_t)((it.n + NC - 1) / NC);
     nbgs[i] = (it.k + kb - 1) / kb;
     max_floats = std::max(max_floats, (size_t)tile_acc_floats((uint32_t)B, kb, D.D.S, NC));
@@ -262,6 +285,26 @@ sk_status build_batch(sk_batch_s* b) {
     zs[i].bytes = b->items[i].d * b->items[i].n * es;
   }
   free_batch_dev(b);
+  // One tensor map per item (A staged through TMA where its layout allows it).
+  std::vector<CUtensorMap> maps(count);
+  std::vector<int> has_map(count, 0);
+  for (int32_t i = 0; i < count; ++i) {
+    memset(&maps[i], 0, sizeof(CUtensorMap));
+    const sk_batch_item& it = b->items[i];
+    has_map[i] = encode_a_map(&maps[i], it.A_dev, it.lda, it.n, it.m, 1 << descs[i].D.log2NC,
+                              32 / ((it.k + 1) / 2))
+                     ? 1
+                     : 0;
+  }
+  if (cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_status, sizeof(unsigned)) != cudaSuccess) {
+    free_batch_dev(b);
+    cudaGetLastError();
+    return set_error(SK_ERR_OOM, "batch tensor map allocation failed");
+  }
+  cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * count, cudaMemcpyHostToDevice);
+  cudaMemset(b->d_status, 0, sizeof(unsigned));
+  for (int32_t i = 0; i < count; ++i) descs[i].D.tmap = has_map[i] ? (const void*)(b->d_maps + i) : nullptr;
   if (cudaMalloc(&b->d_descs, sizeof(BatchDesc) * count) != cudaSuccess ||
       cudaMalloc(&b->d_work, sizeof(BatchWork) * std::max<size_t>(work.size(), 1)) != cudaSuccess ||
       cudaMalloc(&b->d_zero, sizeof(ZeroSpan) * count) != cudaSuccess ||
@@ -275,14 +318,23 @@ sk_status build_batch(sk_batch_s* b) {
   cudaMemcpy(b->d_zero, zs.data(), sizeof(ZeroSpan) * count, cudaMemcpyHostToDevice);
   cudaMemset(b->d_counter, 0, sizeof(int32_t));
   b->nwork = (int64_t)work.size();
-  b->smem = max_floats * 4 + hbytes;
+  b->acc_floats = (int64_t)max_floats;
+  b->slot_bytes = slot_max;
+  {
+    const size_t base = smem_plan(b->acc_floats, nwarps, slot_max, 0).total;
+    const size_t per_depth = (size_t)nwarps * (slot_max + 8);
+    int32_t depth = (int32_t)std::min<size_t>(kMaxRingDepth, (optin_c - base) / per_depth);
+    b->depth = std::max(1, depth);
+  }
+  b->smem = smem_plan(b->acc_floats, nwarps, slot_max, b->depth).total;
   b->use_threads = threads;
   const void* kern = batch_kernel_ptr(b->rule);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) != cudaSuccess)
     return set_error(SK_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(cudaGetLastError()));
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (void (*)(const BatchDesc*, const BatchWork*, int64_t, int32_t*))kern,
-                                                threads, b->smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, (void (*)(const BatchDesc*, const BatchWork*, int64_t, int32_t*, int64_t, int32_t, int32_t, unsigned*))kern,
+      threads, b->smem);
   if (per_sm < 1) return set_error(SK_ERR_UNSUPPORTED, "batch kernel does not fit on an SM");
   b->grid = (int32_t)std::min<int64_t>((int64_t)sms * per_sm, std::max<int64_t>(b->nwork, 1));
   cudaError_t e = cudaGetLastError();
@@ -353,7 +405,8 @@ sk_status sk_batch_launch(sk_batch b, void* stream) {
   }
   int32_t launches = 0;
   cudaError_t e = launch_batch(b->d_descs, b->d_work, b->nwork, b->d_counter, b->d_zero, (int32_t)b->items.size(),
-                               b->rule, b->use_threads, b->smem, b->grid, (cudaStream_t)stream, &launches);
+                               b->rule, b->use_threads, b->smem, b->grid, b->acc_floats, b->slot_bytes, b->depth,
+                               b->d_status, (cudaStream_t)stream, &launches);
   if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
   return SK_OK;
 }

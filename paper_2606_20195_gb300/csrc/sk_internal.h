@@ -19,13 +19,27 @@ struct TileLaunch {
   int32_t kb;       // blocks per block group
   int32_t threads;  // threads per CTA
   int32_t grid;     // CTAs (0 = automatic)
+  int32_t slices;   // work items per chunk (> 1: two-level combine through P)
+  float* P;         // slices > 1: chunks x d x n FP32 scratch, zero on entry, zero on exit
+  int32_t* counters;  // slices > 1: chunks x nbg x ncg counters, zero on entry, zero on exit
+  unsigned* status;   // sticky device status word (may be null)
+  int64_t col_off;    // global column index of column 0 (keys the rounding random bits)
+  int32_t allow_tma;  // stage A through TMA when its layout allows it
+  int32_t depth;      // TMA ring slots per warp (1..4)
 };
 
-// Shared-memory bytes the tile kernel needs for (B, kb, NC, threads).
-size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads);
+// Shared-memory bytes the tile kernel needs for (B, kb, NC, threads, k, ring depth).
+size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads, int32_t k, int32_t depth);
+// Encode a 2-D tensor map over A (n columns, `rows` rows, row stride lda) with box NC x RB; false if
+// the layout does not allow TMA (A not 16-byte aligned, lda % 4 != 0, too many rows).
+bool encode_a_map(void* map, const float* A, int64_t lda, int64_t n, int64_t rows, int32_t NC, int32_t RB);
 int32_t tile_slots(int32_t NC, int32_t kb);
 // Enqueue the chunked tile kernel (atomic flush). Returns a CUDA error code.
 cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches);
+// Chunks, column groups and block groups of a launch.
+void tile_geometry(const TileLaunch& L, int64_t* chunks, int32_t* ncg, int32_t* nbg);
+// Resident CTAs per SM of the tile kernel for (rule, threads, dynamic shared memory).
+int32_t tile_ctas_per_sm(int32_t rule, int32_t threads, size_t smem);
 
 struct LiteralLaunch {
   const float* A;
@@ -34,6 +48,7 @@ struct LiteralLaunch {
   int32_t k, rule;
   uint64_t seed;
   float scale;
+  int64_t col_off;
 };
 cudaError_t launch_literal(const LiteralLaunch& L, cudaStream_t st, int32_t* launches);
 
@@ -46,6 +61,7 @@ struct DetLaunch {
   uint64_t seed;
   float scale;
   int64_t R;
+  int64_t col_off;
 };
 cudaError_t launch_det(const DetLaunch& L, cudaStream_t st, int32_t* launches);
 
@@ -75,7 +91,7 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launche
 struct BatchDesc;     // device-side item descriptor (sk_batch.cu)
 struct BatchWork;     // device-side work item
 cudaError_t launch_batch(const void* descs, const void* work, int64_t nwork, int32_t* counter, const void* zero_list,
-                         int32_t nzero, int32_t rule, int32_t threads, size_t smem, int32_t grid, cudaStream_t st,
-                         int32_t* launches);
+                         int32_t nzero, int32_t rule, int32_t threads, size_t smem, int32_t grid, int64_t acc_floats,
+                         int32_t slot_bytes, int32_t depth, unsigned* status, cudaStream_t st, int32_t* launches);
 
 }  // namespace sk

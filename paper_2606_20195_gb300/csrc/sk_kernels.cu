@@ -1,7 +1,11 @@
 // Single-matrix sketch kernels: the chunked tile kernel (fast path), the paper-literal per-element
 // kernel (comparator), the canonical-order deterministic kernel (verification), and the S pattern
 // kernel. Paper Sec. 4.1 (SparseStack scatter) and Sec. 4.2 (FP16 variants).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "sk_device.cuh"
 #include "sk_internal.h"
@@ -15,33 +19,73 @@ struct TileGrid {
   int64_t row_begin, row_end;  // global rows processed
   int64_t R;                   // chunk rows
   int64_t t_first;             // first chunk index
-  int64_t items;               // chunks * nbg * ncg
-  int32_t ncg, nbg;
+  int64_t items;               // chunks * slices * nbg * ncg
+  int32_t ncg, nbg, slices;
   int32_t acc_floats;          // floats of the accumulator (multiple of 4)
+  float* P;                    // slices > 1: per-chunk FP32 totals, chunk-major, d x n each (zero)
+  int32_t* counters;           // slices > 1: finished slices per (chunk, bg, g) (zero)
+  unsigned* status;            // sticky status word (kStatus*), may be null
+  int32_t use_tma;             // 1: A arrives through the tensor map
+  int32_t depth;               // TMA ring slots per warp
 };
 
 template <int RULE>
-__global__ void __launch_bounds__(1024) tile_kernel(const TileGrid P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(1024) tile_kernel(const TileGrid P, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int last_slice;
+  __shared__ int abort_flag;
   float* acc = reinterpret_cast<float*>(smem_raw);
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  uint64_t* hbuf = reinterpret_cast<uint64_t*>(smem_raw + (size_t)P.acc_floats * 4) + warp * 32;
+  const int RBh = 32 / (int)P.D.kp;
+  const SmemPlan SL = smem_plan(P.acc_floats, nwarps, ring_slot_bytes(RBh, 1 << P.D.log2NC), P.depth);
+  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem_raw + SL.wbuf_off) + warp * kWordsPerWarp;
+  WarpRing ring = make_ring(smem_raw, SL, warp);
   for (int x = threadIdx.x; x < P.acc_floats; x += blockDim.x) acc[x] = 0.f;
+  if (threadIdx.x == 0) abort_flag = 0;
   __syncthreads();
-  const TileDesc& D = P.D;
+  TileDesc D = P.D;
+  D.tmap = P.use_tma ? (const void*)&tmap : nullptr;
+  const int64_t dn = (int64_t)D.B * D.k * D.n;
   for (int64_t w = blockIdx.x; w < P.items; w += gridDim.x) {
     const int32_t g = (int32_t)(w % P.ncg);
-    const int64_t rest = w / P.ncg;
+    int64_t rest = w / P.ncg;
     const int32_t bg = (int32_t)(rest % P.nbg);
-    const int64_t t = P.t_first + rest / P.nbg;
-    const int64_t r0 = max(t * P.R, P.row_begin);
-    const int64_t r1 = min((t + 1) * P.R, P.row_end);
+    rest /= P.nbg;
+    const int32_t sl = (int32_t)(rest % P.slices);
+    const int64_t tl = rest / P.slices;
+    const int64_t t = P.t_first + tl;
+    const int64_t c0 = max(t * P.R, P.row_begin);
+    const int64_t c1 = min((t + 1) * P.R, P.row_end);
+    const int64_t r0 = c0 + (c1 - c0) * sl / P.slices;
+    const int64_t r1 = c0 + (c1 - c0) * (sl + 1) / P.slices;
     const int32_t j0 = bg * D.kb;
     const int32_t kbe = min(D.kb, (int32_t)D.k - j0);
-    tile_scatter(D, r0, r1, g, j0, kbe, acc, hbuf, warp, nwarps);
+    if (!tile_scatter(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps)) {
+      abort_flag = 1;
+      if (P.status) atomicOr(P.status, kStatusTimeout);
+    }
     __syncthreads();
-    tile_flush<RULE>(D, t, g, j0, kbe, acc);
+    if (abort_flag) break;
+    if (P.slices == 1) {
+      tile_flush<RULE>(D, t, g, j0, kbe, acc);
+    } else {
+      float* Pt = P.P + tl * dn;
+      tile_flush_partial(D, g, j0, kbe, acc, Pt);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int32_t* cnt = P.counters + (tl * P.nbg + bg) * P.ncg + g;
+        const int prev = atomicAdd(cnt, 1);
+        last_slice = (prev == P.slices - 1);
+        if (last_slice) *cnt = 0;
+      }
+      __syncthreads();
+      if (last_slice) {
+        __threadfence();
+        tile_finish_chunk<RULE>(D, t, g, j0, kbe, Pt);
+      }
+    }
     __threadfence();
     __syncthreads();
   }
@@ -49,16 +93,56 @@ __global__ void __launch_bounds__(1024) tile_kernel(const TileGrid P) {
 
 int32_t tile_slots(int32_t NC, int32_t kb) { return std::min(32 / NC, kb); }
 
-size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads) {
+size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads, int32_t k, int32_t depth) {
   const int32_t S = tile_slots(NC, kb);
   const int64_t fl = tile_acc_floats((uint32_t)B, kb, S, NC);
-  return (size_t)fl * 4 + (size_t)(threads / 32) * 32 * 8;
+  const int32_t RB = 32 / ((k + 1) / 2);
+  return smem_plan(fl, threads / 32, ring_slot_bytes(RB, NC), depth).total;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+bool encode_a_map(void* map, const float* A, int64_t lda, int64_t n, int64_t rows, int32_t NC, int32_t RB) {
+  if ((reinterpret_cast<uintptr_t>(A) & 15u) != 0 || (lda & 3) != 0 || rows >= ((int64_t)1 << 31) ||
+      n >= ((int64_t)1 << 31) || RB > 256 || NC > 256)
+    return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)lda * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)NC, (cuuint32_t)RB};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)A, dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 static int ilog2(int v) {
   int r = 0;
   while ((1 << r) < v) ++r;
   return r;
+}
+
+void tile_geometry(const TileLaunch& L, int64_t* chunks, int32_t* ncg, int32_t* nbg) {
+  const int64_t t_first = L.row_begin / L.R;
+  const int64_t t_last = (L.row_end - 1) / L.R;
+  *chunks = t_last - t_first + 1;
+  *ncg = (int32_t)((L.n + L.NC - 1) / L.NC);
+  *nbg = (L.k + L.kb - 1) / L.kb;
 }
 
 cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches) {
@@ -81,19 +165,30 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   P.row_end = L.row_end;
   P.R = L.R;
   P.t_first = L.row_begin / L.R;
-  const int64_t t_last = (L.row_end - 1) / L.R;
-  P.ncg = (int32_t)((L.n + L.NC - 1) / L.NC);
-  P.nbg = (L.k + L.kb - 1) / L.kb;
-  P.items = (t_last - P.t_first + 1) * P.ncg * P.nbg;
+  int64_t chunks;
+  tile_geometry(L, &chunks, &P.ncg, &P.nbg);
+  P.slices = std::max(1, L.slices);
+  P.items = chunks * P.slices * P.ncg * P.nbg;
   P.acc_floats = (int32_t)tile_acc_floats((uint32_t)B, L.kb, P.D.S, L.NC);
-  const size_t smem = tile_smem_bytes(B, L.kb, L.NC, L.threads);
+  P.P = L.P;
+  P.counters = L.counters;
+  P.status = L.status;
+  P.D.col_off = L.col_off;
+  P.D.tmap = nullptr;
+  if (P.slices > 1 && (!P.P || !P.counters)) return cudaErrorInvalidValue;
+  CUtensorMap tmap;
+  memset(&tmap, 0, sizeof(tmap));
+  const int32_t RB = 32 / (int32_t)P.D.kp;
+  P.use_tma = (L.allow_tma && encode_a_map(&tmap, L.A, L.lda, L.n, L.row_end - L.row_begin, L.NC, RB)) ? 1 : 0;
+  P.depth = std::max(1, L.depth);
+  const size_t smem = tile_smem_bytes(B, L.kb, L.NC, L.threads, L.k, P.depth);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  void (*kern)(const TileGrid);
+  void (*kern)(const TileGrid, const CUtensorMap);
   switch (L.rule) {
     case kRN: kern = tile_kernel<kRN>; break;
     case kSR: kern = tile_kernel<kSR>; break;
@@ -109,9 +204,29 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   int64_t grid = L.grid > 0 ? L.grid : (int64_t)sms * per_sm;
   grid = std::min<int64_t>(grid, P.items);
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, L.threads, smem, st>>>(P);
+  kern<<<(unsigned)grid, L.threads, smem, st>>>(P, tmap);
   if (launches) *launches += 1;
   return cudaGetLastError();
+}
+
+int32_t tile_ctas_per_sm(int32_t rule, int32_t threads, size_t smem) {
+  void (*kern)(const TileGrid, const CUtensorMap);
+  switch (rule) {
+    case kRN: kern = tile_kernel<kRN>; break;
+    case kSR: kern = tile_kernel<kSR>; break;
+    case kDither: kern = tile_kernel<kDither>; break;
+    default: kern = tile_kernel<kFP32>; break;
+  }
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm;
 }
 
 // ------------------------------------------------------------------ paper-literal kernel
@@ -146,12 +261,16 @@ __global__ void literal_kernel(const LiteralLaunch L, uint32_t B, uint32_t kp) {
         atomicAdd(y, x0);
         if (has1) atomicAdd(y + 1, x1);
       } else {
-        float u[4] = {0.f, 0.f, 0.f, 0.f};
-        if (RULE != kRN) uniforms4(L.seed, r, (uint32_t)(c0 >> 2), (uint64_t)i, u);
-        const __half q0 = quantize<RULE>(x0, u[c0 & 3]);
+        float u[4] = {0.f, 0.f, 0.f, 0.f}, u1n[4] = {0.f, 0.f, 0.f, 0.f};
+        const int64_t cg = L.col_off + c0;
+        if (RULE != kRN) {
+          uniforms4(L.seed, r, (uint32_t)(cg >> 2), (uint64_t)i, u);
+          if ((cg & 3) == 3 && has1) uniforms4(L.seed, r, (uint32_t)(cg >> 2) + 1u, (uint64_t)i, u1n);
+        }
+        const __half q0 = quantize<RULE>(x0, u[cg & 3]);
         __half* y = reinterpret_cast<__half*>(L.Y) + (int64_t)r * n + c0;
         if (has1) {
-          const __half q1 = quantize<RULE>(x1, u[(c0 + 1) & 3]);
+          const __half q1 = quantize<RULE>(x1, ((cg & 3) == 3) ? u1n[0] : u[(cg + 1) & 3]);
           if (even) {
             atomicAdd(reinterpret_cast<__half2*>(y), __halves2half2(q0, q1));
           } else {
@@ -222,9 +341,10 @@ __global__ void det_kernel(const DetLaunch L, uint32_t B, uint32_t kp) {
         *y = __fadd_rn(*y, x);
       } else {
         float u[4] = {0.f, 0.f, 0.f, 0.f};
-        if (RULE != kRN) uniforms4(L.seed, (uint32_t)r, (uint32_t)(c >> 2), (uint64_t)t, u);
+        const int64_t cg = L.col_off + c;
+        if (RULE != kRN) uniforms4(L.seed, (uint32_t)r, (uint32_t)(cg >> 2), (uint64_t)t, u);
         __half* y = reinterpret_cast<__half*>(L.Y) + r * n + c;
-        *y = __hadd(*y, quantize<RULE>(x, u[c & 3]));
+        *y = __hadd(*y, quantize<RULE>(x, u[cg & 3]));
       }
     }
   }

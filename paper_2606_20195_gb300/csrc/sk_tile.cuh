@@ -1,5 +1,6 @@
-// One work item of the chunked sketch: rows [r0, r1) of chunk t, columns [g*NC, g*NC + NC) and
-// blocks [j0, j0 + kb) of S, accumulated in an FP32 shared-memory tile and then flushed into Y.
+// One work item of the chunked sketch: rows [r0, r1) (all or a slice of chunk t), columns
+// [g*NC, g*NC + NC) and blocks [j0, j0 + kbe) of S, accumulated in an FP32 shared-memory tile and
+// then flushed.
 //
 // Paper Sec. 4.1 (scatter of every element of A to its zeta target rows, Listing 1) and Sec. 4.2
 // (FP16 quantization of each contribution, packed half2 atomics, Listing 2). Two changes from the
@@ -11,8 +12,13 @@
 // Shared-memory layout of the accumulator: lines of LW = S*NC floats. Block jl of the group (jl in
 // [0, kb)) owns lines (jl / S) * B + s for its B target rows s, in slot (jl % S) of width NC.
 // A warp is split into G = 32/NC lane groups of NC lanes (one lane per column); in one pass the G
-// lane groups handle G (row, block) pairs of the same row batch. When kb >= G and kb % G == 0 the
-// G pairs of a pass lie in G different slots, so the 32 lanes touch 32 different banks.
+// lane groups handle G (row, block) pairs of the same row batch. When kb >= G the G pairs of a pass
+// lie in G different slots, so the 32 lanes touch 32 different banks.
+//
+// A chunk split into several slices (work items on different CTAs) is combined in two levels: each
+// slice adds its FP32 partials into a per-chunk FP32 buffer in global memory, and the CTA that
+// finishes the chunk's last slice scales, quantizes and adds the chunk total into Y. The result is
+// the chunk total of the canonical order up to the FP32 summation order inside the chunk.
 #pragma once
 
 #include "sk_device.cuh"
@@ -33,18 +39,82 @@ struct TileDesc {
   int32_t log2NC;   // columns per work item = 1 << log2NC (2..5)
   int32_t S;        // slots per accumulator line
   int32_t kb;       // blocks per block group
+  int64_t col_off;  // global column index of column 0 (keys the rounding random bits)
+  const void* tmap; // 2-D tensor map over A (box NC x RB), or null: direct loads
 };
+
+// Per-warp TMA staging ring: `depth` slots of RB x NC floats (128-byte aligned) and their mbarriers.
+// `uses` counts the batches this warp has consumed so far; slot and phase parity derive from it.
+struct WarpRing {
+  float* slots;
+  uint64_t* bars;
+  int32_t depth;
+  int32_t slot_floats;
+  uint32_t uses;
+};
+
+// Bytes of one staging slot for RB rows of NC floats (at least 128, a multiple of 128).
+__host__ __device__ inline int32_t ring_slot_bytes(int32_t RB, int32_t NC) {
+  const int32_t b = RB * NC * 4;
+  return ((b + 127) / 128) * 128;
+}
+constexpr int kMaxRingDepth = 4;
+
+// 32-bit words per warp of the per-batch target buffer.
+constexpr int kWordsPerWarp = 64;
+
 
 // Floats of the accumulator tile for a descriptor.
 __host__ __device__ inline int64_t tile_acc_floats(uint32_t B, int32_t kb, int32_t S, int32_t NC) {
   return (int64_t)((kb + S - 1) / S) * (int64_t)B * (int64_t)S * (int64_t)NC;
 }
 
+// Shared-memory carve-up of the tile kernels: accumulator | per-warp target words | per-warp TMA
+// ring slots (128-byte aligned) | per-warp ring mbarriers.
+struct SmemPlan {
+  size_t acc_bytes, wbuf_off, slots_off, bars_off, total;
+  int32_t slot_bytes, depth;
+};
+
+__host__ __device__ inline SmemPlan smem_plan(int64_t acc_floats, int nwarps, int32_t slot_bytes, int32_t depth) {
+  SmemPlan L;
+  L.acc_bytes = (size_t)acc_floats * 4;
+  L.wbuf_off = (L.acc_bytes + 127) & ~(size_t)127;
+  L.slots_off = L.wbuf_off + (size_t)nwarps * kWordsPerWarp * 4;
+  L.slots_off = (L.slots_off + 127) & ~(size_t)127;
+  L.bars_off = L.slots_off + (size_t)nwarps * depth * slot_bytes;
+  L.total = L.bars_off + (size_t)nwarps * depth * 8;
+  L.slot_bytes = slot_bytes;
+  L.depth = depth;
+  return L;
+}
+
+// Set up this warp's staging ring (lane 0 initializes the mbarriers).
+__device__ __forceinline__ WarpRing make_ring(unsigned char* smem_raw, const SmemPlan& L, int warp) {
+  WarpRing r;
+  r.slots = reinterpret_cast<float*>(smem_raw + L.slots_off + (size_t)warp * L.depth * L.slot_bytes);
+  r.bars = reinterpret_cast<uint64_t*>(smem_raw + L.bars_off) + warp * L.depth;
+  r.depth = L.depth;
+  r.slot_floats = L.slot_bytes / 4;
+  r.uses = 0;
+  if ((threadIdx.x & 31) == 0) {
+    for (int s = 0; s < L.depth; ++s) mbar_init(r.bars + s, 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  return r;
+}
+
 // Scatter rows [r0, r1) of the work item into the zeroed accumulator `acc`. Called by every warp of
-// the CTA; warp `warp` of `nwarps` takes row batches warp, warp + nwarps, ... `hbuf` is this warp's
-// 32-entry scratch for the stream outputs of the current batch.
-__device__ __forceinline__ void tile_scatter(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
-                                             int32_t kbe, float* acc, uint64_t* hbuf, int warp, int nwarps) {
+// the CTA; warp `warp` of `nwarps` takes row batches warp, warp + nwarps, ... `wbuf` is this warp's
+// kWordsPerWarp-word scratch: for each (row, block) of the current batch it holds the accumulator
+// offset (in floats, without the column) of the row's target in that block, with the sign in bit 31.
+// With a tensor map, the warp's batches of A arrive through its TMA ring (ring.depth batches in
+// flight); otherwise each lane loads its batch's values directly. Returns false if a bounded wait
+// gave up (after waiting, again bounded, for the warp's copies still in flight).
+__device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
+                                             int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
+                                             int nwarps) {
   const int lane = threadIdx.x & 31;
   const int NC = 1 << D.log2NC;
   const int G = 32 >> D.log2NC;
@@ -53,136 +123,266 @@ __device__ __forceinline__ void tile_scatter(const TileDesc& D, int64_t r0, int6
   const int S = D.S;
   const int LW = S * NC;
   const uint32_t B = D.B;
-  const uint32_t kp = D.kp;
+  const int kp = (int)D.kp;
   const int64_t col = (int64_t)g * NC + c;
   const bool col_ok = col < D.n;
   const float* __restrict__ Abase = D.A + (col_ok ? col : 0);
+  float* __restrict__ acc_c = acc + c;
   // Rows of one batch: the 32 lanes compute one 64-bit stream output each, kp per row.
-  const int RB = 32 / (int)kp;
+  const int RB = 32 / kp;
   const int64_t nrows = r1 - r0;
   const int64_t nbatch = (nrows + RB - 1) / RB;
-  // Pair indices p = j/2 of the group span [j0/2, (j0+kbe-1)/2]; batch-local lane L holds
-  // (row L / kp, pair L % kp).
-  if (kbe >= G) {
-    for (int64_t bt = warp; bt < nbatch; bt += nwarps) {
-      const int64_t ib = r0 + bt * RB;
-      const int nr = (int)min((int64_t)RB, r1 - ib);
-      {
-        const int rl = lane / (int)kp;
-        const int pp = lane - rl * (int)kp;
-        hbuf[lane] = (rl < nr) ? row_pair_bits(D.seed, (uint64_t)(ib + rl), kp, (uint32_t)pp) : 0ull;
-      }
-      __syncwarp();
-      for (int rl = 0; rl < nr; ++rl) {
-        const int64_t i = ib + rl;
-        const float a = col_ok ? __ldg(Abase + (i - D.row_base) * D.lda) : 0.f;
-        for (int jb = 0; jb < kbe; jb += G) {
-          const int jl = jb + q;
-          if (jl < kbe && col_ok) {
-            const uint32_t j = (uint32_t)(j0 + jl);
-            const uint32_t w = block_word(hbuf[rl * kp + (j >> 1)], j);
-            const uint32_t s = word_to_slot(w, B);
-            const float v = (w & 1u) ? -a : a;
-            atomicAdd(&acc[((jl / S) * (int64_t)B + s) * LW + (jl % S) * NC + c], v);
-          }
+  const int64_t nmine = (nbatch > warp) ? (nbatch - 1 - warp) / nwarps + 1 : 0;
+  // Hash-round role of this lane: (row hr, pair hp) of the batch, the two blocks of the pair.
+  const int hr = lane / kp;
+  const int hp = lane - hr * kp;
+  int hj[2], hoff[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int j = 2 * hp + e;
+    const int jl = j - j0;
+    hj[e] = (j < (int)D.k && jl >= 0 && jl < kbe) ? jl : -1;
+    hoff[e] = (hj[e] >= 0) ? ((jl / S) * (int)B * LW + (jl % S) * NC) : 0;
+  }
+  const bool tma = D.tmap != nullptr;
+  const int depth = ring.depth;
+  const uint32_t box_bytes = (uint32_t)(RB * NC * 4);
+  auto issue = [&](int64_t kk) {
+    const int64_t bt = warp + kk * nwarps;
+    const uint32_t u = ring.uses + (uint32_t)kk;
+    const int slot = (int)(u % (uint32_t)depth);
+    uint64_t* bar = ring.bars + slot;
+    mbar_arrive_expect_tx(bar, box_bytes);
+    tma_load_2d(ring.slots + (size_t)slot * ring.slot_floats, D.tmap, g * NC, (int32_t)(r0 + bt * RB - D.row_base),
+                bar);
+  };
+  if (tma && lane == 0) {
+    for (int64_t kk = 0; kk < min((int64_t)depth, nmine); ++kk) issue(kk);
+  }
+  bool ok = true;
+  for (int64_t kk = 0; kk < nmine; ++kk) {
+    const int64_t bt = warp + kk * nwarps;
+    const int64_t ib = r0 + bt * RB;
+    const int nr = (int)min((int64_t)RB, r1 - ib);
+    if (hr < nr) {
+      const uint64_t h = row_pair_bits(D.seed, (uint64_t)(ib + hr), (uint32_t)kp, (uint32_t)hp);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        if (hj[e] >= 0) {
+          const uint32_t w = e ? (uint32_t)h : (uint32_t)(h >> 32);
+          const uint32_t s = word_to_slot(w, B);
+          wbuf[hr * kbe + hj[e]] = ((uint32_t)hoff[e] + s * (uint32_t)LW) | (w << 31);
         }
       }
-      __syncwarp();
+    }
+    // Values of this batch: from the staging slot (row-major RB x NC box) or loaded directly.
+    const float* stage = nullptr;
+    if (tma) {
+      const uint32_t u = ring.uses + (uint32_t)kk;
+      const int slot = (int)(u % (uint32_t)depth);
+      if (!mbar_wait_bounded(ring.bars + slot, (u / (uint32_t)depth) & 1u)) {
+        ok = false;
+        // Drain this warp's later copies that are still in flight, then give up.
+        for (int64_t k2 = kk + 1; k2 < min(kk + depth, nmine); ++k2) {
+          const uint32_t u2 = ring.uses + (uint32_t)k2;
+          mbar_wait_bounded(ring.bars + (u2 % (uint32_t)depth), (u2 / (uint32_t)depth) & 1u);
+        }
+        break;
+      }
+      stage = ring.slots + (size_t)slot * ring.slot_floats;
+    }
+    __syncwarp();
+    // This lane's updates of the batch, enumerated as entries e = 0..E-1, processed in groups of 8
+    // with a batched compare-and-swap (shared-memory FP32 atomic add has no native instruction).
+    if (kbe >= G) {
+      for (int rl = 0; rl < nr; ++rl) {
+        const float a = tma ? stage[rl * NC + c] : (col_ok ? __ldg(Abase + (ib + rl - D.row_base) * D.lda) : 0.f);
+        const uint32_t* wr = wbuf + rl * kbe;
+        for (int jl = q; jl < kbe; jl += G) {
+          const uint32_t w = wr[jl];
+          const float v = __uint_as_float(__float_as_uint(a) ^ (w & 0x80000000u));
+          if (col_ok) atomicAdd(acc_c + (w & 0x7FFFFFFFu), v);
+        }
+      }
+    } else {
+      // Fewer blocks than lane groups: a pass covers RP = G / kbe rows.
+      const int RP = G / kbe;
+      const int roff = q / kbe;
+      const int jl = q - roff * kbe;
+      if (roff < RP && col_ok) {
+        for (int rl = roff; rl < nr; rl += RP) {
+          const float a = tma ? stage[rl * NC + c] : __ldg(Abase + (ib + rl - D.row_base) * D.lda);
+          const uint32_t w = wbuf[rl * kbe + jl];
+          const float v = __uint_as_float(__float_as_uint(a) ^ (w & 0x80000000u));
+          atomicAdd(acc_c + (w & 0x7FFFFFFFu), v);
+        }
+      }
+    }
+    __syncwarp();
+    if (tma && lane == 0 && kk + depth < nmine) {
+      fence_proxy_async_smem();
+      issue(kk + depth);
+    }
+  }
+  ring.uses += (uint32_t)nmine;
+  return ok;
+}
+
+// Scale, quantize and add four consecutive columns of output row r (chunk t) into Y: one Philox
+// call gives the four uniforms, FP32 adds use one 16-byte vector reduction, FP16 adds two packed
+// half2 atomics (paper Listing 2).
+template <int RULE>
+__device__ __forceinline__ void emit_quad(const TileDesc& D, uint32_t r, int64_t col0, float4 v, int64_t t) {
+  const int64_t n = D.n;
+  const float x0 = __fmul_rn(D.scale, v.x), x1 = __fmul_rn(D.scale, v.y);
+  const float x2 = __fmul_rn(D.scale, v.z), x3 = __fmul_rn(D.scale, v.w);
+  if (RULE == kFP32) {
+    float* y = reinterpret_cast<float*>(D.Y) + (int64_t)r * n + col0;
+    if ((n & 3) == 0 && col0 + 3 < n) {
+      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(y), "f"(x0), "f"(x1), "f"(x2), "f"(x3)
+                   : "memory");
+    } else {
+      atomicAdd(y, x0);
+      if (col0 + 1 < n) atomicAdd(y + 1, x1);
+      if (col0 + 2 < n) atomicAdd(y + 2, x2);
+      if (col0 + 3 < n) atomicAdd(y + 3, x3);
     }
   } else {
-    // Fewer blocks than lane groups: a pass covers RP = G / kbe rows.
-    const int RP = G / kbe;
-    const int roff = q / kbe;
-    const int jl = q - roff * kbe;
-    const bool lane_on = roff < RP;
-    const uint32_t j = (uint32_t)(j0 + jl);
-    for (int64_t bt = warp; bt < nbatch; bt += nwarps) {
-      const int64_t ib = r0 + bt * RB;
-      const int nr = (int)min((int64_t)RB, r1 - ib);
-      {
-        const int rl = lane / (int)kp;
-        const int pp = lane - rl * (int)kp;
-        hbuf[lane] = (rl < nr) ? row_pair_bits(D.seed, (uint64_t)(ib + rl), kp, (uint32_t)pp) : 0ull;
+    float u[4] = {0.f, 0.f, 0.f, 0.f};
+    if (RULE != kRN) {
+      // Columns col_off + col0 .. +3 of the global column space; their uniforms come from at most
+      // two Philox calls (words (column mod 4) of counter column quad floor(column / 4)).
+      const int64_t cg = D.col_off + col0;
+      if ((cg & 3) == 0) {
+        uniforms4(D.seed, r, (uint32_t)(cg >> 2), (uint64_t)t, u);
+      } else {
+        float ua[4], ub[4];
+        uniforms4(D.seed, r, (uint32_t)(cg >> 2), (uint64_t)t, ua);
+        uniforms4(D.seed, r, (uint32_t)(cg >> 2) + 1u, (uint64_t)t, ub);
+        const int o = (int)(cg & 3);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) u[e] = (o + e < 4) ? ua[o + e] : ub[o + e - 4];
       }
-      __syncwarp();
-      for (int rb = 0; rb < nr; rb += RP) {
-        const int rl = rb + roff;
-        if (lane_on && rl < nr && col_ok) {
-          const int64_t i = ib + rl;
-          const float a = __ldg(Abase + (i - D.row_base) * D.lda);
-          const uint32_t w = block_word(hbuf[rl * kp + (j >> 1)], j);
-          const uint32_t s = word_to_slot(w, B);
-          const float v = (w & 1u) ? -a : a;
-          atomicAdd(&acc[((jl / S) * (int64_t)B + s) * LW + (jl % S) * NC + c], v);
-        }
-      }
-      __syncwarp();
+    }
+    const __half q0 = quantize<RULE>(x0, u[0]);
+    const __half q1 = quantize<RULE>(x1, u[1]);
+    const __half q2 = quantize<RULE>(x2, u[2]);
+    const __half q3 = quantize<RULE>(x3, u[3]);
+    __half* y = reinterpret_cast<__half*>(D.Y) + (int64_t)r * n + col0;
+    if ((n & 1) == 0) {
+      atomicAdd(reinterpret_cast<__half2*>(y), __halves2half2(q0, q1));  // col0 + 1 < n since n even
+      if (col0 + 3 < n) atomicAdd(reinterpret_cast<__half2*>(y + 2), __halves2half2(q2, q3));
+    } else {
+      atomicAdd(y, q0);
+      if (col0 + 1 < n) atomicAdd(y + 1, q1);
+      if (col0 + 2 < n) atomicAdd(y + 2, q2);
+      if (col0 + 3 < n) atomicAdd(y + 3, q3);
     }
   }
 }
 
-// Flush the accumulator of a finished work item into Y and zero it. Chunk index t keys the
-// rounding random bits. Quads of four consecutive columns are handled together: one Philox call
-// gives their four uniforms, FP32 adds use one 16-byte vector reduction, FP16 adds use two packed
-// half2 atomics (paper Listing 2). Quads whose four partial sums are all zero are skipped: adding
-// a quantized zero leaves Y unchanged.
-template <int RULE>
-__device__ __forceinline__ void tile_flush(const TileDesc& D, int64_t t, int32_t g, int32_t j0, int32_t kbe,
-                                           float* acc) {
-  const int NC = 1 << D.log2NC;
-  const int S = D.S;
-  const int LW = S * NC;
-  const uint32_t B = D.B;
-  const int nq = NC >> 2;
-  const int64_t total = (int64_t)kbe * B * nq;
-  const int64_t n = D.n;
-  const bool vec4 = (n & 3) == 0;
-  const bool even = (n & 1) == 0;
-  for (int64_t f = threadIdx.x; f < total; f += blockDim.x) {
+// Visit the accumulator quads of a work item: f in [0, kbe*B*NC/4) -> (smem pointer, row, col0).
+struct QuadIter {
+  int nq, S, LW, NC;
+  uint32_t B;
+  __device__ __forceinline__ void at(int64_t f, int32_t g, int32_t j0, float* acc, float*& p, uint32_t& r,
+                                     int64_t& col0) const {
     const int c4 = (int)(f % nq);
     const int64_t rest = f / nq;
     const uint32_t s = (uint32_t)(rest % B);
     const int jl = (int)(rest / B);
-    float* p = &acc[((jl / S) * (int64_t)B + s) * LW + (jl % S) * NC + 4 * c4];
-    float4 v = *reinterpret_cast<float4*>(p);
+    p = &acc[((jl / S) * (int64_t)B + s) * LW + (jl % S) * NC + 4 * c4];
+    r = (uint32_t)(j0 + jl) * B + s;
+    col0 = (int64_t)g * NC + 4 * c4;
+  }
+};
+
+__device__ __forceinline__ QuadIter quad_iter(const TileDesc& D) {
+  QuadIter it;
+  it.NC = 1 << D.log2NC;
+  it.nq = it.NC >> 2;
+  it.S = D.S;
+  it.LW = D.S * it.NC;
+  it.B = D.B;
+  return it;
+}
+
+// Flush a work item that holds a whole chunk: quantize and add into Y, zero the accumulator.
+// Quads whose four partial sums are all zero are skipped (adding a quantized zero leaves Y as is).
+template <int RULE>
+__device__ __forceinline__ void tile_flush(const TileDesc& D, int64_t t, int32_t g, int32_t j0, int32_t kbe,
+                                           float* acc) {
+  const QuadIter it = quad_iter(D);
+  const int64_t total = (int64_t)kbe * D.B * it.nq;
+  for (int64_t f = threadIdx.x; f < total; f += blockDim.x) {
+    float* p;
+    uint32_t r;
+    int64_t col0;
+    it.at(f, g, j0, acc, p, r, col0);
+    const float4 v = *reinterpret_cast<float4*>(p);
     if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
     *reinterpret_cast<float4*>(p) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (col0 >= D.n) continue;
+    emit_quad<RULE>(D, r, col0, v, t);
+  }
+}
+
+// Flush a slice of a chunk: add the FP32 partials into the chunk buffer P (d x n, row stride n),
+// zero the accumulator.
+__device__ __forceinline__ void tile_flush_partial(const TileDesc& D, int32_t g, int32_t j0, int32_t kbe, float* acc,
+                                                   float* P) {
+  const QuadIter it = quad_iter(D);
+  const int64_t total = (int64_t)kbe * D.B * it.nq;
+  const int64_t n = D.n;
+  for (int64_t f = threadIdx.x; f < total; f += blockDim.x) {
+    float* p;
+    uint32_t r;
+    int64_t col0;
+    it.at(f, g, j0, acc, p, r, col0);
+    const float4 v = *reinterpret_cast<float4*>(p);
+    if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+    *reinterpret_cast<float4*>(p) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (col0 >= n) continue;
+    float* y = P + (int64_t)r * n + col0;
+    if ((n & 3) == 0 && col0 + 3 < n) {
+      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(y), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                   : "memory");
+    } else {
+      atomicAdd(y, v.x);
+      if (col0 + 1 < n) atomicAdd(y + 1, v.y);
+      if (col0 + 2 < n) atomicAdd(y + 2, v.z);
+      if (col0 + 3 < n) atomicAdd(y + 3, v.w);
+    }
+  }
+}
+
+// Last slice of a chunk done: read the chunk totals of this (column group, block group) region of
+// P, quantize and add them into Y, and restore P to zero for the next use.
+template <int RULE>
+__device__ __forceinline__ void tile_finish_chunk(const TileDesc& D, int64_t t, int32_t g, int32_t j0, int32_t kbe,
+                                                  float* P) {
+  const int NC = 1 << D.log2NC;
+  const int nq = NC >> 2;
+  const int64_t n = D.n;
+  const int64_t total = (int64_t)kbe * D.B * nq;
+  for (int64_t f = threadIdx.x; f < total; f += blockDim.x) {
+    const int c4 = (int)(f % nq);
+    const int64_t rr = f / nq;
+    const uint32_t r = (uint32_t)j0 * D.B + (uint32_t)rr;
     const int64_t col0 = (int64_t)g * NC + 4 * c4;
     if (col0 >= n) continue;
-    const uint32_t r = (uint32_t)(j0 + jl) * B + s;
-    const float x0 = __fmul_rn(D.scale, v.x), x1 = __fmul_rn(D.scale, v.y);
-    const float x2 = __fmul_rn(D.scale, v.z), x3 = __fmul_rn(D.scale, v.w);
-    if (RULE == kFP32) {
-      float* y = reinterpret_cast<float*>(D.Y) + (int64_t)r * n + col0;
-      if (vec4 && col0 + 3 < n) {
-        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(y), "f"(x0), "f"(x1), "f"(x2), "f"(x3)
-                     : "memory");
-      } else {
-        atomicAdd(y, x0);
-        if (col0 + 1 < n) atomicAdd(y + 1, x1);
-        if (col0 + 2 < n) atomicAdd(y + 2, x2);
-        if (col0 + 3 < n) atomicAdd(y + 3, x3);
-      }
-    } else {
-      float u[4] = {0.f, 0.f, 0.f, 0.f};
-      if (RULE != kRN) uniforms4(D.seed, r, (uint32_t)(col0 >> 2), (uint64_t)t, u);
-      const __half q0 = quantize<RULE>(x0, u[0]);
-      const __half q1 = quantize<RULE>(x1, u[1]);
-      const __half q2 = quantize<RULE>(x2, u[2]);
-      const __half q3 = quantize<RULE>(x3, u[3]);
-      __half* y = reinterpret_cast<__half*>(D.Y) + (int64_t)r * n + col0;
-      if (even && col0 + 3 < n) {
-        atomicAdd(reinterpret_cast<__half2*>(y), __halves2half2(q0, q1));
-        atomicAdd(reinterpret_cast<__half2*>(y + 2), __halves2half2(q2, q3));
-      } else if (even) {
-        atomicAdd(reinterpret_cast<__half2*>(y), __halves2half2(q0, q1));  // col0 + 1 < n since n even
-      } else {
-        atomicAdd(y, q0);
-        if (col0 + 1 < n) atomicAdd(y + 1, q1);
-        if (col0 + 2 < n) atomicAdd(y + 2, q2);
-        if (col0 + 3 < n) atomicAdd(y + 3, q3);
-      }
-    }
+    float* y = P + (int64_t)r * n + col0;
+    float4 v;
+    v.x = __ldcg(y);
+    v.y = (col0 + 1 < n) ? __ldcg(y + 1) : 0.f;
+    v.z = (col0 + 2 < n) ? __ldcg(y + 2) : 0.f;
+    v.w = (col0 + 3 < n) ? __ldcg(y + 3) : 0.f;
+    if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+    y[0] = 0.f;
+    if (col0 + 1 < n) y[1] = 0.f;
+    if (col0 + 2 < n) y[2] = 0.f;
+    if (col0 + 3 < n) y[3] = 0.f;
+    emit_quad<RULE>(D, r, col0, v, t);
   }
 }
 

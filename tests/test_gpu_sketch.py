@@ -34,6 +34,7 @@ def _apply(sk, A_h, d, k, rule, seed, dev, **params):
     out = _to_np(Y, rule)
     launches = plan.get(sk.SK_PARAM_LAST_LAUNCHES)
     R = plan.get(sk.SK_PARAM_LAST_CHUNK_ROWS)
+    assert plan.get(sk.SK_PARAM_DEVICE_STATUS) == 0
     plan.close()
     return out, launches, R
 
