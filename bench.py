@@ -195,6 +195,116 @@ def run_reference(args, world, rank):
     return 0
 
 
+def bench_solve(dev, rules=(0, 1, 2, 3), m=1 << 24, n=128, d=2048, k=8, reps=3):
+    """Sketch-and-solve at the coherent least-squares shape: phase times and residual ratios."""
+    import torch
+    from paper_2606_20195_gb300 import inputs, sk
+    A = inputs.device_matrix(m, n, "coherent", seed=3, device=str(dev))
+    g = torch.Generator(device=dev)
+    g.manual_seed(4)
+    xs = torch.randn(n, generator=g, device=dev, dtype=torch.float64)
+    b = (A.double() @ xs + 1e-6 * torch.randn(m, generator=g, device=dev, dtype=torch.float64)).float()
+    # FP64 least-squares optimum for the ratio (torch on the GPU, reporting only)
+    Rr = torch.linalg.qr(torch.cat([A.double(), b.double()[:, None]], dim=1), mode="r").R
+    r_opt = float(abs(Rr[n, n]))
+    out = {}
+    for rule in rules:
+        plan = sk.Plan(d, m, k, rule, seed=11)
+        x = torch.empty(n, dtype=torch.float32, device=dev)
+        Y = torch.empty((d, n), dtype=torch.float32 if rule == 0 else torch.float16, device=dev)
+        for _ in range(2):
+            plan.solve(A, b, x)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ts, tk = [], []
+        for _ in range(reps):
+            ev[0].record()
+            plan.solve(A, b, x)
+            ev[1].record()
+            plan.apply(A, Y)
+            ev[2].record()
+            torch.cuda.synchronize()
+            ts.append(ev[0].elapsed_time(ev[1]))
+            tk.append(ev[1].elapsed_time(ev[2]))
+        status, kappa = plan.solve_status()
+        res = float(torch.linalg.vector_norm(A.double() @ x.double() - b.double()))
+        out[list(sk.RULES)[rule]] = {"solve_ms": statistics.median(ts), "sketch_A_ms": statistics.median(tk),
+                                     "qr_and_Sb_ms": statistics.median(ts) - statistics.median(tk),
+                                     "residual_ratio": res / r_opt, "kappa_SA_diag_estimate": kappa,
+                                     "status": status}
+        plan.close()
+    del A, b
+    torch.cuda.empty_cache()
+    return {"workload": f"coherent LS m={m} n={n} d={d} k={k}", **out}
+
+
+def bench_batch(dev, rule_name="fp16_rn", count=256, reps=5):
+    """256 uneven matrices in one persistent launch, captured in a CUDA graph and replayed."""
+    import torch
+    from paper_2606_20195_gb300 import autotune, inputs, sk
+    rule = sk.RULES[rule_name]
+    items = []
+    total = 0
+    for i, (m, n, fam) in enumerate(inputs.batch_shapes(count, seed=0)):
+        A = inputs.device_matrix(m, n, fam, seed=100 + i, device=str(dev))
+        Y = torch.empty((32 * n, n), dtype=torch.float32 if rule == 0 else torch.float16, device=dev)
+        items.append({"A": A, "Y": Y, "m": m, "n": n, "d": 32 * n, "k": 4, "seed": i})
+        total += m * n * 4 + 32 * n * n * (4 if rule == 0 else 2)
+    b, params = autotune.tune_batch(items, rule, reps=2)
+    nwork, bytes_a = sk.sk_batch_info(b)
+    stream = torch.cuda.Stream(device=dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        sk.sk_batch_launch(b, stream)
+    stream.synchronize()
+    with torch.cuda.graph(graph, stream=stream):
+        sk.sk_batch_launch(b, torch.cuda.current_stream(dev))
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        graph.replay()
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / reps
+    sk.sk_batch_destroy(b)
+    del items
+    torch.cuda.empty_cache()
+    return {"workload": f"{count} uneven matrices, m log-uniform [2^12,2^20], n in 8..128, d=32n, k=4, {rule_name}",
+            "GB/s": total / (ms * 1e-3) / 1e9, "ms": ms, "work_items": nwork, "bytes_A": bytes_a,
+            "tuned": params, "graph": True}
+
+
+def bench_serve(dev, count=60, log2_m=(14, 20), seed=0):
+    """Poisson stream of sketch-and-solve requests: continuous batching vs one at a time."""
+    from paper_2606_20195_gb300 import serve
+    base_reqs = serve.make_stream(count, rate_hz=0.0, seed=seed, log2_m=log2_m)
+    one = serve.Server(slots=1, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
+    one.run_one_at_a_time(serve.make_stream(count, rate_hz=0.0, seed=seed, log2_m=log2_m))
+    cap = one.run_one_at_a_time(base_reqs)
+    capacity = cap["solves_per_s"]
+    one.close()
+    out = {"workload": f"Poisson sketch-and-solve requests, m log-uniform [2^{log2_m[0]},2^{log2_m[1]}], "
+                       f"n in 16..256, d=16n, k in {{1,4,8}}, 4 rules, 120 GB budget, 8 slots",
+           "one_at_a_time_back_to_back": cap}
+    for frac in (0.5, 0.8, 0.95):
+        reqs = serve.make_stream(count, rate_hz=frac * capacity, seed=seed, log2_m=log2_m)
+        srv = serve.Server(slots=8, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
+        # warm-up pass over the same shapes (plan scratch and per-stream allocator pools)
+        srv.run(serve.make_stream(count, rate_hz=frac * capacity, seed=seed, log2_m=log2_m))
+        cb = srv.run(reqs)
+        srv.close()
+        reqs1 = serve.make_stream(count, rate_hz=frac * capacity, seed=seed, log2_m=log2_m)
+        s1 = serve.Server(slots=1, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
+        s1.run_one_at_a_time(serve.make_stream(count, rate_hz=0.0, seed=seed, log2_m=log2_m))
+        fifo = s1.run_one_at_a_time(reqs1)
+        s1.close()
+        out[f"rate_{int(frac * 100)}pct"] = {"rate_hz": frac * capacity, "continuous": cb, "fifo": fifo}
+    return out
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,7 +313,9 @@ def main() -> int:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--rule", default="fp16_rn", choices=["fp32", "fp16_rn", "fp16_sr", "fp16_dither"])
-    ap.add_argument("--no-extras", action="store_true", help="skip variants, distortion, cpu baseline")
+    ap.add_argument("--no-extras", action="store_true", help="skip variants, distortion, cpu baseline, serving")
+    ap.add_argument("--extras", default="serve",
+                    help="comma list of extra measurements: serve (default), solve, batch, all")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_init()
@@ -318,6 +430,17 @@ def main() -> int:
         extras["fp16_vs_fp32_speedup"] = variants["fp16_rn"]["GB/s"] / variants["fp32"]["GB/s"]
         gb, cores, sample = cpu_oracle_rate(m, n, d, k, budget_s=10.0)
         cpu_baseline = {"value": gb, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample}
+        want = set(args.extras.split(",")) if args.extras else set()
+        if "all" in want:
+            want = {"serve", "solve", "batch"}
+        del A_pin
+        if "serve" in want:
+            extras["serving"] = bench_serve(dev)
+            extras["p99_solve_ms"] = extras["serving"]["rate_80pct"]["continuous"]["p99_ms"]
+        if "solve" in want:
+            extras["sketch_and_solve"] = bench_solve(dev)
+        if "batch" in want:
+            extras["batched"] = bench_batch(dev)
 
     if rank == 0:
         line = {

@@ -112,9 +112,10 @@ __device__ __forceinline__ WarpRing make_ring(unsigned char* smem_raw, const Sme
 // With a tensor map, the warp's batches of A arrive through its TMA ring (ring.depth batches in
 // flight); otherwise each lane loads its batch's values directly. Returns false if a bounded wait
 // gave up (after waiting, again bounded, for the warp's copies still in flight).
-__device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
-                                             int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
-                                             int nwarps) {
+template <int PPR>
+__device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
+                                               int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
+                                               int nwarps) {
   const int lane = threadIdx.x & 31;
   const int NC = 1 << D.log2NC;
   const int G = 32 >> D.log2NC;
@@ -194,7 +195,22 @@ __device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int6
     __syncwarp();
     // This lane's updates of the batch, enumerated as entries e = 0..E-1, processed in groups of 8
     // with a batched compare-and-swap (shared-memory FP32 atomic add has no native instruction).
-    if (kbe >= G) {
+    if (PPR > 0 && tma) {
+      // Fast path: PPR (row, block) passes per row, unrolled. Columns past n read TMA zero fill,
+      // so their lanes add zeros into accumulator columns that are never flushed.
+#pragma unroll 2
+      for (int rl = 0; rl < nr; ++rl) {
+        const float a = stage[rl * NC + c];
+        const uint32_t* wr = wbuf + rl * kbe + q;
+#pragma unroll
+        for (int pp = 0; pp < (PPR > 0 ? PPR : 1); ++pp) {
+          if (pp * G + q < kbe) {
+            const uint32_t w = wr[pp * G];
+            atomicAdd(acc_c + (w & 0x7FFFFFFFu), __uint_as_float(__float_as_uint(a) ^ (w & 0x80000000u)));
+          }
+        }
+      }
+    } else if (kbe >= G) {
       for (int rl = 0; rl < nr; ++rl) {
         const float a = tma ? stage[rl * NC + c] : (col_ok ? __ldg(Abase + (ib + rl - D.row_base) * D.lda) : 0.f);
         const uint32_t* wr = wbuf + rl * kbe;
@@ -226,6 +242,21 @@ __device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int6
   }
   ring.uses += (uint32_t)nmine;
   return ok;
+}
+
+// Dispatch on the passes per row of the work item (blocks per lane group) for the unrolled path.
+__device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
+                                             int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
+                                             int nwarps) {
+  const int G = 32 >> D.log2NC;
+  const int ppr = (kbe >= G) ? (kbe + G - 1) / G : 0;
+  switch (ppr) {
+    case 1: return tile_scatter_t<1>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+    case 2: return tile_scatter_t<2>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+    case 4: return tile_scatter_t<4>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+    case 8: return tile_scatter_t<8>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+    default: return tile_scatter_t<0>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+  }
 }
 
 // Scale, quantize and add four consecutive columns of output row r (chunk t) into Y: one Philox
