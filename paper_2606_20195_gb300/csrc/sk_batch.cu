@@ -91,6 +91,15 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchDesc* __restrict
   }
 }
 
+static const void* batch_kernel_ptr(int rule) {
+  switch (rule) {
+    case kRN: return (const void*)batch_kernel<kRN>;
+    case kSR: return (const void*)batch_kernel<kSR>;
+    case kDither: return (const void*)batch_kernel<kDither>;
+    default: return (const void*)batch_kernel<kFP32>;
+  }
+}
+
 cudaError_t launch_batch(const void* descs, const void* work, int64_t nwork, int32_t* counter, const void* zero_list,
                          int32_t nzero, int32_t rule, int32_t threads, size_t smem, int32_t grid, int64_t acc_floats,
                          int32_t slot_bytes, int32_t depth, unsigned* status, cudaStream_t st, int32_t* launches) {
@@ -101,6 +110,9 @@ cudaError_t launch_batch(const void* descs, const void* work, int64_t nwork, int
   if (e != cudaSuccess) return e;
   const BatchDesc* dd = reinterpret_cast<const BatchDesc*>(descs);
   const BatchWork* ww = reinterpret_cast<const BatchWork*>(work);
+  // The dynamic shared-memory limit is per-kernel state that another batch may have lowered.
+  e = cudaFuncSetAttribute(batch_kernel_ptr(rule), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   switch (rule) {
     case kRN: batch_kernel<kRN><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
     case kSR: batch_kernel<kSR><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
@@ -109,15 +121,6 @@ cudaError_t launch_batch(const void* descs, const void* work, int64_t nwork, int
   }
   if (launches) *launches += 1;
   return cudaGetLastError();
-}
-
-static const void* batch_kernel_ptr(int rule) {
-  switch (rule) {
-    case kRN: return (const void*)batch_kernel<kRN>;
-    case kSR: return (const void*)batch_kernel<kSR>;
-    case kDither: return (const void*)batch_kernel<kDither>;
-    default: return (const void*)batch_kernel<kFP32>;
-  }
 }
 
 }  // namespace sk
