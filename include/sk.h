@@ -195,6 +195,28 @@ SK_API sk_status sk_batch_launch(sk_batch batch, void* stream);
 SK_API sk_status sk_batch_info(sk_batch batch, int64_t* work_items, int64_t* bytes_A);
 SK_API void sk_batch_destroy(sk_batch batch);
 
+/*
+ * sk_apply_noalloc — the same result as sk_apply in SK_MODE_ATOMIC (same kernel, same chunking),
+ * for callers that must not allocate device memory: code running where cudaMalloc is forbidden or
+ * unsafe (inside an allocator or memory-pool callback, a real-time or fixed-footprint service whose
+ * memory is budgeted up front, an embedding application that owns all device memory). The paper has
+ * no counterpart; this is an interface variant of the sketch call.
+ *
+ * Instead of plan-owned scratch, the kernel's scratch (per-chunk FP32 totals, slice counters and the
+ * status word) lives in one fixed static device array of 16 MiB in this library. The caller still
+ * passes A and Y exactly as for sk_apply. The call allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine; it only enqueues memsets and the kernel on `stream`.
+ *   - The first call on each device looks up the device address of that array
+ *     (cudaGetSymbolAddress) with the device current; make that first call before any stream
+ *     capture on the device.
+ *   - Sizes whose scratch exceeds 16 MiB (chunks x d x n x 4 bytes when chunks are split across CTAs)
+ *     are rejected with SK_ERR_UNSUPPORTED and a message; use sk_apply for those.
+ *   - Every call on a device shares the one array: calls that overlap on the GPU (different streams,
+ *     or different host threads) race and give wrong results. Serialize them on one stream.
+ *   - Only SK_MODE_ATOMIC with the tile kernel is supported (SK_ERR_UNSUPPORTED otherwise).
+ */
+SK_API sk_status sk_apply_noalloc(sk_plan plan, const float* A_dev, int64_t lda, int64_t n, void* Y_dev, void* stream);
+
 /* Release the plan and its device scratch (synchronizes the device first). NULL is a no-op. */
 SK_API void sk_destroy(sk_plan plan);
 

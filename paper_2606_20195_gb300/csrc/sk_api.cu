@@ -679,3 +679,53 @@ void sk_destroy(sk_plan p) {
 }
 
 }  // extern "C"
+
+namespace sk {
+
+// Tile-kernel launch description for sk_apply_noalloc (sk_noalloc.cu): the same configuration
+// sk_apply's atomic tile path chooses, with no scratch attached. Allocates nothing.
+sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, int64_t n, void* Y, TileLaunch* L) {
+  sk_status s = validate_apply(p, A, lda, n, Y);
+  if (s != SK_OK) return s;
+  if (p->mode != SK_MODE_ATOMIC || p->kernel == SK_KERNEL_LITERAL)
+    return set_error(SK_ERR_UNSUPPORTED, "sk_apply_noalloc runs the atomic-mode tile kernel only");
+  DevInfo di;
+  s = dev_info(&di);
+  if (s != SK_OK) return s;
+  TileCfg cfg;
+  s = choose_tile(p, n, p->m, di, &cfg);
+  if (s != SK_OK) return s;
+  L->A = A;
+  L->Y = Y;
+  L->lda = lda;
+  L->n = n;
+  L->row_begin = p->row_offset;
+  L->row_end = p->row_offset + p->m;
+  L->d = p->d;
+  L->k = p->k;
+  L->rule = p->rule;
+  L->seed = p->seed;
+  L->scale = p->scale;
+  L->R = cfg.R;
+  L->NC = cfg.NC;
+  L->kb = cfg.kb;
+  L->threads = cfg.threads;
+  L->grid = cfg.grid;
+  L->slices = cfg.slices;
+  L->depth = cfg.depth;
+  L->col_off = 0;
+  L->allow_tma = 1;
+  L->status = nullptr;
+  L->P = nullptr;
+  L->counters = nullptr;
+  return SK_OK;
+}
+
+size_t noalloc_elem_size(const sk_plan_s* p) { return elem_size(p->rule); }
+
+void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R) {
+  p->last_launches = launches;
+  p->last_R = R;
+}
+
+}  // namespace sk

@@ -1,0 +1,86 @@
+// sk_apply_noalloc: the atomic-mode sketch with its scratch in a fixed static device array, for
+// callers that cannot allocate device memory (allocator callbacks, fixed-footprint services,
+// applications that own all device memory). Contract and limits: include/sk.h.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "../../include/sk.h"
+#include "sk_hostutil.h"
+#include "sk_internal.h"
+
+namespace sk {
+sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, int64_t n, void* Y, TileLaunch* L);
+size_t noalloc_elem_size(const sk_plan_s* p);
+void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R);
+}  // namespace sk
+
+using namespace sk;
+
+namespace {
+
+// 16 MiB of scratch, held by every GPU that loads this library until the process exits.
+constexpr size_t kScratchBytes = (size_t)16 << 20;
+constexpr size_t kStatusBytes = 256;            // status word, padded
+constexpr size_t kCounterBytes = (size_t)64 << 10;  // slice counters
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once per device).
+sk_status scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(SK_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return set_error(SK_ERR_CUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+    g_scratch_addr[dev] = ptr;
+  }
+  *out = g_scratch_addr[dev];
+  return SK_OK;
+}
+
+}  // namespace
+
+extern "C" SK_API sk_status sk_apply_noalloc(sk_plan p, const float* A, int64_t lda, int64_t n, void* Y,
+                                             void* stream) {
+  clear_error();
+  TileLaunch L;
+  sk_status s = noalloc_tile_launch(p, A, lda, n, Y, &L);
+  if (s != SK_OK) return s;
+  void* base = nullptr;
+  s = scratch_address(&base);
+  if (s != SK_OK) return s;
+  int64_t chunks;
+  int32_t ncg, nbg;
+  tile_geometry(L, &chunks, &ncg, &nbg);
+  const size_t need_counters = sizeof(int32_t) * (size_t)(chunks * ncg * nbg);
+  const size_t need_P = (L.slices > 1) ? sizeof(float) * (size_t)chunks * (size_t)(L.d * L.n) : 0;
+  if (need_counters > kCounterBytes || kStatusBytes + kCounterBytes + need_P > kScratchBytes)
+    return set_error(SK_ERR_UNSUPPORTED,
+                     "sk_apply_noalloc: this size needs %zu bytes of scratch, above the %zu-byte static array; "
+                     "use sk_apply",
+                     kStatusBytes + kCounterBytes + need_P, kScratchBytes);
+  unsigned char* b = static_cast<unsigned char*>(base);
+  cudaStream_t st = (cudaStream_t)stream;
+  // The array keeps the previous call's contents: clear what this call needs at zero.
+  cudaError_t e = cudaMemsetAsync(Y, 0, noalloc_elem_size(p) * (size_t)(L.d * L.n), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, kStatusBytes + need_counters, st);
+  if (e == cudaSuccess && need_P) e = cudaMemsetAsync(b + kStatusBytes + kCounterBytes, 0, need_P, st);
+  if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "zeroing: %s", cudaGetErrorString(e));
+  L.status = reinterpret_cast<unsigned*>(b);
+  L.counters = reinterpret_cast<int32_t*>(b + kStatusBytes);
+  L.P = need_P ? reinterpret_cast<float*>(b + kStatusBytes + kCounterBytes) : nullptr;
+  int32_t launches = 0;
+  e = launch_tile(L, st, &launches);
+  if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "tile kernel launch: %s", cudaGetErrorString(e));
+  noalloc_record(p, launches, L.R);
+  return SK_OK;
+}

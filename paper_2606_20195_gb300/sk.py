@@ -26,6 +26,7 @@ EXPORTS = [
     "sk_version", "sk_last_error", "sk_plan_create", "sk_plan_set", "sk_plan_get", "sk_apply",
     "sk_apply_host", "sk_solve", "sk_solve_status", "sk_materialize_S", "sk_batch_create",
     "sk_batch_set", "sk_batch_launch", "sk_batch_info", "sk_batch_destroy", "sk_destroy",
+    "sk_apply_noalloc",
 ]
 
 
@@ -87,6 +88,8 @@ def load(path: str | None = None):
     L.sk_batch_destroy.argtypes = [vp]
     L.sk_destroy.restype = None
     L.sk_destroy.argtypes = [vp]
+    L.sk_apply_noalloc.restype = st
+    L.sk_apply_noalloc.argtypes = [vp, vp, i64, i64, vp, vp]
     _lib = L
     return L
 
@@ -197,6 +200,13 @@ def sk_batch_destroy(batch: int) -> None:
 
 def sk_destroy(plan: int) -> None:
     load().sk_destroy(plan)
+
+
+def sk_apply_noalloc(plan: int, A, lda: int, n: int, Y, stream=None) -> None:
+    """sk_apply for callers that cannot allocate device memory: the kernel's scratch is a fixed
+    16 MiB static device array of the library (see include/sk.h for the limits and the rule that
+    calls overlapping on the GPU race)."""
+    check(load().sk_apply_noalloc(plan, _ptr(A), lda, n, _ptr(Y), _stream_handle(stream)))
 
 
 # ----------------------------------------------------------------------------- convenience wrapper
