@@ -392,6 +392,17 @@ def main() -> int:
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = world * bytes_step / float(te.item()) / 1e9
+    # context for e2e: plain pinned host -> device copy bandwidth of A
+    A_scratch = torch.empty_like(A)
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    A_scratch.copy_(A_pin, non_blocking=True)
+    h0.record(stream)
+    for _ in range(3):
+        A_scratch.copy_(A_pin, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbps = 3 * m * n * 4 / (h0.elapsed_time(h1) * 1e-3) / 1e9
+    del A_scratch
 
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs")
@@ -454,7 +465,8 @@ def main() -> int:
             "roofline": roofline,
             "cpu_baseline": cpu_baseline,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": m * n * 4,
-                    "d2h_bytes_per_step": d * n * es, "launches_per_step": e2e_launches},
+                    "d2h_bytes_per_step": d * n * es, "launches_per_step": e2e_launches,
+                    "pinned_h2d_copy_GBps": h2d_gbps},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             **extras,

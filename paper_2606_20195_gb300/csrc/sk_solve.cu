@@ -4,10 +4,11 @@
 //
 // One cooperative launch factors W = [SA | Sb] (d x (n+1)) by Householder reflections. The d rows
 // are split across the CTAs (one per SM at most); each CTA keeps its rows of W in shared memory
-// for the whole factorization. Column step j needs two grid-wide reductions (the norm of column j
-// below the diagonal, then v^T W[:, c] for the trailing columns), done with FP64 atomics into
-// per-step buffers and separated by grid barriers. Row j of R is final after step j and is written
-// to global memory by its owner; CTA 0 finishes with the back substitution R x = (Q^T Sb)[:n].
+// for the whole factorization. Column step j needs one grid-wide reduction: the partial sums of
+// x^T x and x^T W[:, c] (x = column j below the diagonal) give both the reflector and v^T W[:, c],
+// accumulated with FP64 atomics into per-step buffers, followed by one grid barrier. The owner of row j
+// publishes that row before the barrier; after the last step every owner writes its final rows of R
+// and CTA 0 finishes with the back substitution R x = (Q^T Sb)[:n].
 //
 // Every grid barrier spins with an iteration limit: on expiry the kernel sets kStatusTimeout in
 // the status word and all CTAs leave at the next check, so a stalled launch cannot hang the GPU.
@@ -22,7 +23,7 @@ namespace sk {
 
 namespace {
 
-constexpr long long kSpinLimit = 1ll << 24;  // iterations of ~100 ns sleeps (~2 s)
+constexpr long long kSpinLimit = 1ll << 26;  // iterations of short sleeps (a few seconds)
 
 // Grid barrier for a co-resident (cooperative) grid. bar[0]: arrivals, bar[1]: generation.
 // Returns false if this CTA, or any CTA before it, gave up waiting.
@@ -47,7 +48,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) 
         }
         // Another CTA already gave up: stop waiting.
         if ((spins & 1023) == 0 && (*(volatile unsigned*)status & kStatusTimeout)) break;
-        __nanosleep(100);
+        __nanosleep(20);
       }
     }
     __threadfence();
@@ -108,7 +109,9 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
   }
   __syncthreads();
   for (int64_t j = 0; j < n; ++j) {
-    // Phase A: squared norm of column j over rows >= j; owner of row j publishes W[j][j].
+    // One grid reduction per column: with x = W[j:, j] and v = x - alpha e_j, both ||x||^2 and
+    // v^T W[:, c] = x^T W[:, c] - alpha W[j][c] follow from the partial sums of x^T x and x^T W[:, c]
+    // over each CTA's rows; the owner of row j also publishes that row.
     double ss = 0.0;
     for (int64_t rl = threadIdx.x; rl < nown; rl += blockDim.x) {
       if (row0 + rl >= j) {
@@ -117,15 +120,24 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
       }
     }
     ss = block_sum(ss, red);
-    if (threadIdx.x == 0) {
-      if (ss != 0.0) atomicAdd(&a.nrm[j], ss);
-      if (j >= row0 && j < row0 + nown) L.bcast[j] = Wl[(j - row0) * ldw + j];
+    if (threadIdx.x == 0 && ss != 0.0) atomicAdd(&a.nrm[j], ss);
+    for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x) {
+      double dot = 0.0;
+      for (int64_t rl = 0; rl < nown; ++rl) {
+        if (row0 + rl < j) continue;
+        dot += Wl[rl * ldw + j] * Wl[rl * ldw + c];
+      }
+      if (dot != 0.0) atomicAdd(&a.wv[j * ldw + c], dot);
+    }
+    if (j >= row0 && j < row0 + nown) {
+      const int64_t rl = j - row0;
+      for (int64_t c = j + threadIdx.x; c <= n; c += blockDim.x) L.R[j * ldw + c] = Wl[rl * ldw + c];
     }
     if (!grid_barrier(L.bar, nb, L.status)) return;
-    // Phase B: reflector v = x - alpha e_j (alpha = -sign(x0) ||x||), partial v^T W[:, c].
+    // Reflector: alpha = -sign(x0) ||x||, v_j = x0 - alpha, tau = 2 / v^T v.
     if (threadIdx.x == 0) {
       const double norm2 = __ldcg(&a.nrm[j]);
-      const double x0 = __ldcg(&L.bcast[j]);
+      const double x0 = __ldcg(&L.R[j * ldw + j]);
       const double alpha = -copysign(sqrt(norm2), x0);
       const double vj = x0 - alpha;
       const double vtv = (norm2 - x0 * x0) + vj * vj;
@@ -135,40 +147,30 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
     }
     __syncthreads();
     const double alpha = sc[0], vj = sc[1], tau = sc[2];
-    if (tau != 0.0) {
-      for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x) {
-        double dot = 0.0;
-        for (int64_t rl = 0; rl < nown; ++rl) {
-          const int64_t r = row0 + rl;
-          if (r < j) continue;
-          const double vr = (r == j) ? vj : Wl[rl * ldw + j];
-          dot += vr * Wl[rl * ldw + c];
-        }
-        if (dot != 0.0) atomicAdd(&a.wv[j * ldw + c], dot);
-      }
-    }
-    if (!grid_barrier(L.bar, nb, L.status)) return;
-    // Phase C: W[r][c] -= tau * v_r * w_c on own rows r >= j, columns c > j.
+    // W[r][c] -= tau v_r w_c with w_c = v^T W[:, c] = x^T W[:, c] - alpha W[j][c].
     if (tau != 0.0) {
       const int64_t ncols = n - j;  // columns j+1 .. n
       for (int64_t e = threadIdx.x; e < nown * ncols; e += blockDim.x) {
         const int64_t rl = e / ncols, c = j + 1 + (e - rl * ncols);
         const int64_t r = row0 + rl;
         if (r < j) continue;
+        const double wc = __ldcg(&a.wv[j * ldw + c]) - alpha * __ldcg(&L.R[j * ldw + c]);
         const double vr = (r == j) ? vj : Wl[rl * ldw + j];
-        Wl[rl * ldw + c] -= tau * vr * __ldcg(&a.wv[j * ldw + c]);
+        Wl[rl * ldw + c] -= tau * vr * wc;
       }
     }
     __syncthreads();
     if (j >= row0 && j < row0 + nown) {
       const int64_t rl = j - row0;
-      if (threadIdx.x == 0) {
-        Wl[rl * ldw + j] = alpha;
-        L.R[j * ldw + j] = alpha;
-      }
-      for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x) L.R[j * ldw + c] = Wl[rl * ldw + c];
+      if (threadIdx.x == 0) Wl[rl * ldw + j] = alpha;
     }
     __syncthreads();
+  }
+  // Final R rows: each owner rewrites its rows of R (diagonal alpha, updated off-diagonals).
+  if (!grid_barrier(L.bar, nb, L.status)) return;
+  for (int64_t jr = row0; jr < row0 + nown && jr < n; ++jr) {
+    const int64_t rl = jr - row0;
+    for (int64_t c = jr + threadIdx.x; c <= n; c += blockDim.x) L.R[jr * ldw + c] = Wl[rl * ldw + c];
   }
   if (!grid_barrier(L.bar, nb, L.status)) return;
   if (b != 0) return;
