@@ -97,7 +97,7 @@ size_t elem_size(int32_t rule) { return rule == SK_FP32 ? 4 : 2; }
 
 // Tile-kernel configuration for a plan and a column count.
 struct TileCfg {
-  int32_t NC = 0, kb = 0, threads = 0, grid = 0, slices = 1, depth = 1;
+  int32_t NC = 0, kb = 0, threads = 0, grid = 0, slices = 1, depth = 1, mb = 1;
   int64_t R = 0;
   bool serial = false;
 };
@@ -146,8 +146,16 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
     return set_error(SK_ERR_UNSUPPORTED,
                      "tile kernel: a block of %lld rows does not fit in shared memory with the requested width",
                      (long long)p->B);
+  // Several hash rounds per TMA box when every work item takes the unrolled fast path (one block
+  // group, kb >= lane groups, a power-of-two number of passes per row): boxes of up to 1 KiB.
+  const int32_t G = 32 / NC;
+  const int32_t ppr = (kb >= G) ? (kb + G - 1) / G : 0;
+  int32_t mb = 1;
+  if (!serial && kb == p->k && (ppr == 1 || ppr == 2 || ppr == 4 || ppr == 8))
+    mb = std::max(1, std::min(8, 1024 / (RB * NC * 4)));
+  while (mb > 1 && tile_smem_bytes(p->B, kb, NC, threads, p->k, 1, mb) > optin) mb /= 2;
   int32_t depth = 1;
-  while (depth < kMaxRingDepth && tile_smem_bytes(p->B, kb, NC, threads, p->k, depth + 1) <= optin) ++depth;
+  while (depth < kMaxRingDepth && tile_smem_bytes(p->B, kb, NC, threads, p->k, depth + 1, mb) <= optin) ++depth;
   int64_t R = p->R > 0 ? p->R : default_chunk_rows(p->m);
   int32_t slices = 1;
   if (!serial) {
@@ -156,7 +164,7 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
     const int64_t ncg = (n + NC - 1) / NC;
     const int64_t nbg = (p->k + kb - 1) / kb;
     const int64_t chunks = (rows + R - 1) / R + 1;
-    const int32_t cps = tile_ctas_per_sm(p->rule, threads, tile_smem_bytes(p->B, kb, NC, threads, p->k, depth));
+    const int32_t cps = tile_ctas_per_sm(p->rule, threads, tile_smem_bytes(p->B, kb, NC, threads, p->k, depth, mb));
     const int64_t target = 4 * (int64_t)di.sms * std::max(cps, 1);
     const int64_t per_chunk = std::max<int64_t>(1, (target + chunks * ncg * nbg - 1) / (chunks * ncg * nbg));
     const int64_t min_rows = std::max<int64_t>(4096, 2 * p->d);
@@ -170,6 +178,7 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
   cfg->R = R;
   cfg->slices = slices;
   cfg->depth = depth;
+  cfg->mb = mb;
   cfg->serial = serial;
   return SK_OK;
 }
@@ -278,6 +287,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
   L.grid = cfg.grid;
   L.slices = cfg.slices;
   L.depth = cfg.depth;
+  L.mb = cfg.mb;
   L.col_off = col_off;
   L.allow_tma = 1;
   if (!p->dstatus) {
@@ -713,6 +723,7 @@ sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, i
   L->grid = cfg.grid;
   L->slices = cfg.slices;
   L->depth = cfg.depth;
+  L->mb = cfg.mb;
   L->col_off = 0;
   L->allow_tma = 1;
   L->status = nullptr;

@@ -26,10 +26,11 @@ struct TileLaunch {
   int64_t col_off;    // global column index of column 0 (keys the rounding random bits)
   int32_t allow_tma;  // stage A through TMA when its layout allows it
   int32_t depth;      // TMA ring slots per warp (1..4)
+  int32_t mb;         // hash rounds per TMA box (1, or more when every work item takes the fast path)
 };
 
-// Shared-memory bytes the tile kernel needs for (B, kb, NC, threads, k, ring depth).
-size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads, int32_t k, int32_t depth);
+// Shared-memory bytes the tile kernel needs for (B, kb, NC, threads, k, ring depth, rounds per box).
+size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads, int32_t k, int32_t depth, int32_t mb = 1);
 // Encode a 2-D tensor map over A (n columns, `rows` rows, row stride lda) with box NC x RB; false if
 // the layout does not allow TMA (A not 16-byte aligned, lda % 4 != 0, too many rows).
 bool encode_a_map(void* map, const float* A, int64_t lda, int64_t n, int64_t rows, int32_t NC, int32_t RB);

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(1024) tile_kernel(const TileGrid P, const __gr
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const int RBh = 32 / (int)P.D.kp;
-  const SmemPlan SL = smem_plan(P.acc_floats, nwarps, ring_slot_bytes(RBh, 1 << P.D.log2NC), P.depth);
+  const SmemPlan SL = smem_plan(P.acc_floats, nwarps, ring_slot_bytes(RBh * P.D.mb, 1 << P.D.log2NC), P.depth);
   uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem_raw + SL.wbuf_off) + warp * kWordsPerWarp;
   WarpRing ring = make_ring(smem_raw, SL, warp);
   for (int x = threadIdx.x; x < P.acc_floats; x += blockDim.x) acc[x] = 0.f;
@@ -93,11 +93,11 @@ __global__ void __launch_bounds__(1024) tile_kernel(const TileGrid P, const __gr
 
 int32_t tile_slots(int32_t NC, int32_t kb) { return std::min(32 / NC, kb); }
 
-size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads, int32_t k, int32_t depth) {
+size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads, int32_t k, int32_t depth, int32_t mb) {
   const int32_t S = tile_slots(NC, kb);
   const int64_t fl = tile_acc_floats((uint32_t)B, kb, S, NC);
   const int32_t RB = 32 / ((k + 1) / 2);
-  return smem_plan(fl, threads / 32, ring_slot_bytes(RB, NC), depth).total;
+  return smem_plan(fl, threads / 32, ring_slot_bytes(RB * mb, NC), depth).total;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
@@ -179,9 +179,10 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   CUtensorMap tmap;
   memset(&tmap, 0, sizeof(tmap));
   const int32_t RB = 32 / (int32_t)P.D.kp;
-  P.use_tma = (L.allow_tma && encode_a_map(&tmap, L.A, L.lda, L.n, L.row_end - L.row_begin, L.NC, RB)) ? 1 : 0;
+  P.D.mb = std::max(1, L.mb);
+  P.use_tma = (L.allow_tma && encode_a_map(&tmap, L.A, L.lda, L.n, L.row_end - L.row_begin, L.NC, RB * P.D.mb)) ? 1 : 0;
   P.depth = std::max(1, L.depth);
-  const size_t smem = tile_smem_bytes(B, L.kb, L.NC, L.threads, L.k, P.depth);
+  const size_t smem = tile_smem_bytes(B, L.kb, L.NC, L.threads, L.k, P.depth, P.D.mb);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

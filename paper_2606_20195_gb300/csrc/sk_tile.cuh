@@ -40,7 +40,8 @@ struct TileDesc {
   int32_t S;        // slots per accumulator line
   int32_t kb;       // blocks per block group
   int64_t col_off;  // global column index of column 0 (keys the rounding random bits)
-  const void* tmap; // 2-D tensor map over A (box NC x RB), or null: direct loads
+  const void* tmap; // 2-D tensor map over A (box NC x RB*mb), or null: direct loads
+  int32_t mb;       // hash rounds (of RB = 32/kp rows) per TMA box
 };
 
 // Per-warp TMA staging ring: `depth` slots of RB x NC floats (128-byte aligned) and their mbarriers.
@@ -244,19 +245,133 @@ __device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, in
   return ok;
 }
 
+// TMA fast path (kb >= G): each warp takes boxes of SB = RB*mb rows (row boxes warp, warp + nwarps,
+// ...), ring.depth of them in flight through its mbarrier ring; inside a box, mb hash rounds of RB
+// rows each; PPR (row, block) passes per row, unrolled. Slot and phase parity advance incrementally.
+// Columns past n read TMA zero fill, so those lanes add zeros into accumulator columns that are never
+// flushed. Returns false if a bounded wait gave up (after draining this warp's copies in flight).
+template <int PPR>
+__device__ __forceinline__ bool tile_scatter_tma(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
+                                                 int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
+                                                 int nwarps) {
+  const int lane = threadIdx.x & 31;
+  const int NC = 1 << D.log2NC;
+  const int G = 32 >> D.log2NC;
+  const int q = lane >> D.log2NC;
+  const int c = lane & (NC - 1);
+  const int S = D.S;
+  const int LW = S * NC;
+  const uint32_t B = D.B;
+  const int kp = (int)D.kp;
+  float* __restrict__ acc_c = acc + c;
+  const int RB = 32 / kp;
+  const int SB = RB * D.mb;
+  const int32_t nrows = (int32_t)(r1 - r0);
+  const int32_t nbox = (nrows + SB - 1) / SB;
+  const int32_t nmine = (nbox > warp) ? (nbox - 1 - warp) / nwarps + 1 : 0;
+  const int hr = lane / kp;
+  const int hp = lane - hr * kp;
+  int hj[2];
+  uint32_t hoff[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int j = 2 * hp + e;
+    const int jl = j - j0;
+    hj[e] = (j < (int)D.k && jl >= 0 && jl < kbe) ? jl : -1;
+    hoff[e] = (hj[e] >= 0) ? (uint32_t)((jl / S) * (int)B * LW + (jl % S) * NC) : 0u;
+  }
+  const int depth = ring.depth;
+  const uint32_t box_bytes = (uint32_t)(SB * NC * 4);
+  const int32_t ybase = (int32_t)(r0 - D.row_base);
+  const int xcol = g * NC;
+  int slot = (int)(ring.uses % (uint32_t)depth);
+  uint32_t par = (ring.uses / (uint32_t)depth) & 1u;
+  if (lane == 0) {
+    int s2 = slot;
+    for (int32_t kk = 0; kk < min(depth, nmine); ++kk) {
+      mbar_arrive_expect_tx(ring.bars + s2, box_bytes);
+      tma_load_2d(ring.slots + (size_t)s2 * ring.slot_floats, D.tmap, xcol, ybase + (warp + kk * nwarps) * SB,
+                  ring.bars + s2);
+      s2 = (s2 + 1 == depth) ? 0 : s2 + 1;
+    }
+  }
+  bool ok = true;
+  for (int32_t kk = 0; kk < nmine; ++kk) {
+    const int32_t box0 = (warp + kk * nwarps) * SB;  // first row of the box, relative to r0
+    if (!mbar_wait_bounded(ring.bars + slot, par)) {
+      ok = false;
+      int s2 = slot;
+      uint32_t p2 = par;
+      for (int32_t k2 = kk + 1; k2 < min(kk + depth, nmine); ++k2) {
+        s2 = (s2 + 1 == depth) ? 0 : s2 + 1;
+        if (s2 == 0) p2 ^= 1u;
+        mbar_wait_bounded(ring.bars + s2, p2);
+      }
+      break;
+    }
+    const float* stage = ring.slots + (size_t)slot * ring.slot_floats;
+    for (int hb = 0; hb < D.mb; ++hb) {
+      const int32_t rb0 = box0 + hb * RB;
+      const int nr = min(RB, nrows - rb0);
+      if (nr <= 0) break;
+      if (hr < nr) {
+        const uint64_t h = row_pair_bits(D.seed, (uint64_t)(r0 + rb0 + hr), (uint32_t)kp, (uint32_t)hp);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (hj[e] >= 0) {
+            const uint32_t w = e ? (uint32_t)h : (uint32_t)(h >> 32);
+            wbuf[hr * kbe + hj[e]] = (hoff[e] + word_to_slot(w, B) * (uint32_t)LW) | (w << 31);
+          }
+        }
+      }
+      __syncwarp();
+      const float* st = stage + hb * RB * NC + c;
+#pragma unroll 2
+      for (int rl = 0; rl < nr; ++rl) {
+        const float a = st[rl * NC];
+        const uint32_t* wr = wbuf + rl * kbe + q;
+#pragma unroll
+        for (int pp = 0; pp < PPR; ++pp) {
+          if (pp * G + q < kbe) {
+            const uint32_t w = wr[pp * G];
+            atomicAdd(acc_c + (w & 0x7FFFFFFFu), __uint_as_float(__float_as_uint(a) ^ (w & 0x80000000u)));
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == 0 && kk + depth < nmine) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(ring.bars + slot, box_bytes);
+      tma_load_2d(ring.slots + (size_t)slot * ring.slot_floats, D.tmap, xcol,
+                  ybase + (warp + (kk + depth) * nwarps) * SB, ring.bars + slot);
+    }
+    slot = (slot + 1 == depth) ? 0 : slot + 1;
+    if (slot == 0) par ^= 1u;
+  }
+  ring.uses += (uint32_t)nmine;
+  return ok;
+}
+
 // Dispatch on the passes per row of the work item (blocks per lane group) for the unrolled path.
 __device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
                                              int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
                                              int nwarps) {
   const int G = 32 >> D.log2NC;
   const int ppr = (kbe >= G) ? (kbe + G - 1) / G : 0;
-  switch (ppr) {
-    case 1: return tile_scatter_t<1>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
-    case 2: return tile_scatter_t<2>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
-    case 4: return tile_scatter_t<4>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
-    case 8: return tile_scatter_t<8>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
-    default: return tile_scatter_t<0>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+  // Boxes of several hash rounds (mb > 1) are only set up by the host when every work item takes the
+  // fast path; anything else would wait for bytes that never come, so refuse it.
+  if (D.tmap != nullptr && D.mb > 1 && !(ppr == 1 || ppr == 2 || ppr == 4 || ppr == 8)) return false;
+  if (D.tmap != nullptr) {
+    switch (ppr) {
+      case 1: return tile_scatter_tma<1>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+      case 2: return tile_scatter_tma<2>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+      case 4: return tile_scatter_tma<4>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+      case 8: return tile_scatter_tma<8>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+      default: break;
+    }
   }
+  return tile_scatter_t<0>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
 }
 
 // Scale, quantize and add four consecutive columns of output row r (chunk t) into Y: one Philox
