@@ -100,6 +100,7 @@ struct TileCfg {
   int32_t NC = 0, kb = 0, threads = 0, grid = 0, slices = 1, depth = 1, mb = 1;
   int64_t R = 0;
   bool serial = false;
+  bool lr = false;
 };
 
 // Default chunk length: at most 8 chunks per matrix (each output then receives at most 8 rounded
@@ -146,13 +147,11 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
     return set_error(SK_ERR_UNSUPPORTED,
                      "tile kernel: a block of %lld rows does not fit in shared memory with the requested width",
                      (long long)p->B);
-  // Several hash rounds per TMA box when every work item takes the unrolled fast path (one block
-  // group, kb >= lane groups, a power-of-two number of passes per row): boxes of up to 1 KiB.
-  const int32_t G = 32 / NC;
-  const int32_t ppr = (kb >= G) ? (kb + G - 1) / G : 0;
+  // One block group (outside serial mode): every work item takes the lane-row path, with several
+  // hash rounds per TMA box (boxes of up to 1 KiB).
+  const bool lr = !serial && kb == p->k;
   int32_t mb = 1;
-  if (!serial && kb == p->k && (ppr == 1 || ppr == 2 || ppr == 4 || ppr == 8))
-    mb = std::max(1, std::min(8, 1024 / (RB * NC * 4)));
+  if (lr) mb = std::max(1, std::min(8, 1024 / (RB * NC * 4)));
   while (mb > 1 && tile_smem_bytes(p->B, kb, NC, threads, p->k, 1, mb) > optin) mb /= 2;
   int32_t depth = 1;
   while (depth < kMaxRingDepth && tile_smem_bytes(p->B, kb, NC, threads, p->k, depth + 1, mb) <= optin) ++depth;
@@ -179,6 +178,7 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
   cfg->slices = slices;
   cfg->depth = depth;
   cfg->mb = mb;
+  cfg->lr = lr;
   cfg->serial = serial;
   return SK_OK;
 }
@@ -288,6 +288,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
   L.slices = cfg.slices;
   L.depth = cfg.depth;
   L.mb = cfg.mb;
+  L.lr = cfg.lr ? 1 : 0;
   L.col_off = col_off;
   L.allow_tma = 1;
   if (!p->dstatus) {
@@ -724,6 +725,7 @@ sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, i
   L->slices = cfg.slices;
   L->depth = cfg.depth;
   L->mb = cfg.mb;
+  L->lr = cfg.lr ? 1 : 0;
   L->col_off = 0;
   L->allow_tma = 1;
   L->status = nullptr;

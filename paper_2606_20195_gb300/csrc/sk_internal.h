@@ -27,6 +27,7 @@ struct TileLaunch {
   int32_t allow_tma;  // stage A through TMA when its layout allows it
   int32_t depth;      // TMA ring slots per warp (1..4)
   int32_t mb;         // hash rounds per TMA box (1, or more when every work item takes the fast path)
+  int32_t lr = 0;     // 1: lane-row scatter (one block group; used only when A is staged through TMA)
 };
 
 // Shared-memory bytes the tile kernel needs for (B, kb, NC, threads, k, ring depth, rounds per box).

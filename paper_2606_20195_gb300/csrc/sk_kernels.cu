@@ -181,6 +181,7 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   const int32_t RB = 32 / (int32_t)P.D.kp;
   P.D.mb = std::max(1, L.mb);
   P.use_tma = (L.allow_tma && encode_a_map(&tmap, L.A, L.lda, L.n, L.row_end - L.row_begin, L.NC, RB * P.D.mb)) ? 1 : 0;
+  P.D.lr = (P.use_tma && L.lr && L.kb == L.k) ? 1 : 0;
   P.depth = std::max(1, L.depth);
   const size_t smem = tile_smem_bytes(B, L.kb, L.NC, L.threads, L.k, P.depth, P.D.mb);
   int dev = 0;

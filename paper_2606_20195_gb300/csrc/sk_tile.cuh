@@ -42,6 +42,7 @@ struct TileDesc {
   int64_t col_off;  // global column index of column 0 (keys the rounding random bits)
   const void* tmap; // 2-D tensor map over A (box NC x RB*mb), or null: direct loads
   int32_t mb;       // hash rounds (of RB = 32/kp rows) per TMA box
+  int32_t lr;       // 1: every work item holds all k blocks and takes the lane-row TMA path
 };
 
 // Per-warp TMA staging ring: `depth` slots of RB x NC floats (128-byte aligned) and their mbarriers.
@@ -353,10 +354,129 @@ __device__ __forceinline__ bool tile_scatter_tma(const TileDesc& D, int64_t r0, 
   return ok;
 }
 
-// Dispatch on the passes per row of the work item (blocks per lane group) for the unrolled path.
+// Shared-memory FP32 reduction (no result); `addr` is a shared-window byte address.
+__device__ __forceinline__ void red_shared_f32(uint32_t addr, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v));
+}
+
+// Lane-row TMA path, for work items that hold all k blocks (j0 = 0, kbe = k). Within a hash round of
+// RB = 32/kp rows, lane (r, hp) owns row r and the pair of blocks (2hp, 2hp+1): it computes that
+// pair's 64-bit stream output, keeps both targets and signs in registers and adds its row's NC values
+// into both targets, column (c + r) mod NC at step c. A lane-dependent flip decides which block of the
+// pair comes first. With S*NC = 32 floats per line, the 32 lanes of one access then differ in
+// (slot mod S, column) and hit 32 distinct banks whenever kp = S and RB <= NC (k = 8 with NC = 8,
+// for example); other shapes stay correct with some bank conflicts. No per-update target word is
+// read from shared memory and no warp-level exchange is needed, so a round is straight-line code.
+// Boxes, ring and bounded waits are as in tile_scatter_tma. Columns past n read TMA zero fill and
+// add zeros into accumulator columns that are never flushed.
+template <int NC>
+__device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, float* acc,
+                                                WarpRing& ring, int warp, int nwarps) {
+  const int lane = threadIdx.x & 31;
+  const int S = D.S;
+  const uint32_t LW = (uint32_t)(S * NC);
+  const uint32_t B = D.B;
+  const int kp = (int)D.kp;
+  const int RB = 32 / kp;
+  const int SB = RB * D.mb;
+  const int r = lane / kp;
+  const int hp = lane - r * kp;
+  const int flip = ((2 * hp) / S + r / NC) & 1;
+  const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
+  uint32_t base[2];
+  bool bv[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int j = 2 * hp + (e ^ flip);
+    bv[e] = r < RB && j < (int)D.k;
+    base[e] = acc_s + 4u * ((uint32_t)(j / S) * B * LW + (uint32_t)((j % S) * NC));
+  }
+  const int32_t nrows = (int32_t)(r1 - r0);
+  const int32_t nbox = (nrows + SB - 1) / SB;
+  const int32_t nmine = (nbox > warp) ? (nbox - 1 - warp) / nwarps + 1 : 0;
+  const int depth = ring.depth;
+  const uint32_t box_bytes = (uint32_t)(SB * NC * 4);
+  const int32_t ybase = (int32_t)(r0 - D.row_base);
+  const int xcol = g * NC;
+  int slot = (int)(ring.uses % (uint32_t)depth);
+  uint32_t par = (ring.uses / (uint32_t)depth) & 1u;
+  if (lane == 0) {
+    int s2 = slot;
+    for (int32_t kk = 0; kk < min(depth, nmine); ++kk) {
+      mbar_arrive_expect_tx(ring.bars + s2, box_bytes);
+      tma_load_2d(ring.slots + (size_t)s2 * ring.slot_floats, D.tmap, xcol, ybase + (warp + kk * nwarps) * SB,
+                  ring.bars + s2);
+      s2 = (s2 + 1 == depth) ? 0 : s2 + 1;
+    }
+  }
+  bool ok = true;
+  for (int32_t kk = 0; kk < nmine; ++kk) {
+    const int32_t box0 = (warp + kk * nwarps) * SB;  // first row of the box, relative to r0
+    if (!mbar_wait_bounded(ring.bars + slot, par)) {
+      ok = false;
+      int s2 = slot;
+      uint32_t p2 = par;
+      for (int32_t k2 = kk + 1; k2 < min(kk + depth, nmine); ++k2) {
+        s2 = (s2 + 1 == depth) ? 0 : s2 + 1;
+        if (s2 == 0) p2 ^= 1u;
+        mbar_wait_bounded(ring.bars + s2, p2);
+      }
+      break;
+    }
+    const float* stage = ring.slots + (size_t)slot * ring.slot_floats;
+    const int32_t nr_box = min(SB, nrows - box0);
+    for (int hb = 0; hb < D.mb; ++hb) {
+      const int rr = hb * RB + r;  // row of the box
+      if (r < RB && rr < nr_box) {
+        const uint64_t h = row_pair_bits(D.seed, (uint64_t)(r0 + box0 + rr), (uint32_t)kp, (uint32_t)hp);
+        uint32_t ad[2], sg[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const uint32_t w = (e ^ flip) ? (uint32_t)h : (uint32_t)(h >> 32);
+          ad[e] = base[e] + 4u * word_to_slot(w, B) * LW;
+          sg[e] = w << 31;
+        }
+        const float* arow = stage + rr * NC;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const uint32_t col = (uint32_t)(c + r) & (uint32_t)(NC - 1);
+          const uint32_t a = __float_as_uint(arow[col]);
+          if (bv[0]) red_shared_f32(ad[0] + 4u * col, __uint_as_float(a ^ sg[0]));
+          if (bv[1]) red_shared_f32(ad[1] + 4u * col, __uint_as_float(a ^ sg[1]));
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && kk + depth < nmine) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(ring.bars + slot, box_bytes);
+      tma_load_2d(ring.slots + (size_t)slot * ring.slot_floats, D.tmap, xcol,
+                  ybase + (warp + (kk + depth) * nwarps) * SB, ring.bars + slot);
+    }
+    slot = (slot + 1 == depth) ? 0 : slot + 1;
+    if (slot == 0) par ^= 1u;
+  }
+  ring.uses += (uint32_t)nmine;
+  return ok;
+}
+
+// Dispatch: the lane-row path when the host set it up, else on the passes per row of the work item
+// (blocks per lane group) for the unrolled path.
 __device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
                                              int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
                                              int nwarps) {
+  if (D.lr) {
+    // Set up by the host only for one block group with a tensor map; refuse anything else, since its
+    // boxes would not match what the host encoded.
+    if (D.tmap == nullptr || j0 != 0 || kbe != (int32_t)D.k) return false;
+    switch (D.log2NC) {
+      case 2: return tile_scatter_lr<4>(D, r0, r1, g, acc, ring, warp, nwarps);
+      case 3: return tile_scatter_lr<8>(D, r0, r1, g, acc, ring, warp, nwarps);
+      case 4: return tile_scatter_lr<16>(D, r0, r1, g, acc, ring, warp, nwarps);
+      case 5: return tile_scatter_lr<32>(D, r0, r1, g, acc, ring, warp, nwarps);
+      default: return false;
+    }
+  }
   const int G = 32 >> D.log2NC;
   const int ppr = (kbe >= G) ? (kbe + G - 1) / G : 0;
   // Boxes of several hash rounds (mb > 1) are only set up by the host when every work item takes the
