@@ -24,9 +24,12 @@ __device__ __forceinline__ uint64_t splitmix_finalize(uint64_t z) {
   return z;
 }
 
+// SplitMix64 state increment (the golden-ratio gamma).
+constexpr uint64_t kSplitMixGamma = 0x9E3779B97F4A7C15ull;
+
 // Output number `idx` (idx >= 1) of the SplitMix64 stream started at `seed`.
 __device__ __forceinline__ uint64_t splitmix_output(uint64_t seed, uint64_t idx) {
-  return splitmix_finalize(seed + idx * 0x9E3779B97F4A7C15ull);
+  return splitmix_finalize(seed + idx * kSplitMixGamma);
 }
 
 // The 64 bits serving blocks 2p and 2p+1 of input row i: stream output i*kp + p + 1, kp = ceil(k/2).

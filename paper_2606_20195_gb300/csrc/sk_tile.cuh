@@ -359,6 +359,32 @@ __device__ __forceinline__ void red_shared_f32(uint32_t addr, float v) {
   asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v));
 }
 
+// One hash round of the lane-row path for lane (r, hp): its row's values at
+// `arow` (NC floats of the staged box), the lane's two blocks at accumulator byte addresses base[e]
+// (target row and column still to add). PRED = false is the straight-line form for rounds in which
+// every lane holds a row and both its blocks exist.
+// `z` is the SplitMix64 state of the lane's stream output (seed + index * golden gamma).
+template <int NC, bool PRED>
+__device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int r, int flip, const float* arow,
+                                         const uint32_t base[2], const bool bv[2], uint32_t LW) {
+  const uint64_t h = splitmix_finalize(z);
+  uint32_t ad[2], sg[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const uint32_t w = (e ^ flip) ? (uint32_t)h : (uint32_t)(h >> 32);
+    ad[e] = base[e] + 4u * word_to_slot(w, D.B) * LW;
+    sg[e] = w << 31;
+  }
+  // (a partial unroll at NC = 32 keeps the loads in flight within the register budget)
+#pragma unroll(NC > 16 ? 8 : NC)
+  for (int c = 0; c < NC; ++c) {
+    const uint32_t col = (uint32_t)(c + r) & (uint32_t)(NC - 1);
+    const uint32_t a = __float_as_uint(arow[col]);
+    if (!PRED || bv[0]) red_shared_f32(ad[0] + 4u * col, __uint_as_float(a ^ sg[0]));
+    if (!PRED || bv[1]) red_shared_f32(ad[1] + 4u * col, __uint_as_float(a ^ sg[1]));
+  }
+}
+
 // Lane-row TMA path, for work items that hold all k blocks (j0 = 0, kbe = k). Within a hash round of
 // RB = 32/kp rows, lane (r, hp) owns row r and the pair of blocks (2hp, 2hp+1): it computes that
 // pair's 64-bit stream output, keeps both targets and signs in registers and adds its row's NC values
@@ -391,6 +417,8 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
     bv[e] = r < RB && j < (int)D.k;
     base[e] = acc_s + 4u * ((uint32_t)(j / S) * B * LW + (uint32_t)((j % S) * NC));
   }
+  // Every lane holds a row of a full round and both its blocks exist (warp-uniform).
+  const bool full_lanes = (RB * kp == 32) && ((D.k & 1u) == 0);
   const int32_t nrows = (int32_t)(r1 - r0);
   const int32_t nbox = (nrows + SB - 1) / SB;
   const int32_t nmine = (nbox > warp) ? (nbox - 1 - warp) / nwarps + 1 : 0;
@@ -425,25 +453,17 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
     }
     const float* stage = ring.slots + (size_t)slot * ring.slot_floats;
     const int32_t nr_box = min(SB, nrows - box0);
-    for (int hb = 0; hb < D.mb; ++hb) {
-      const int rr = hb * RB + r;  // row of the box
-      if (r < RB && rr < nr_box) {
-        const uint64_t h = row_pair_bits(D.seed, (uint64_t)(r0 + box0 + rr), (uint32_t)kp, (uint32_t)hp);
-        uint32_t ad[2], sg[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const uint32_t w = (e ^ flip) ? (uint32_t)h : (uint32_t)(h >> 32);
-          ad[e] = base[e] + 4u * word_to_slot(w, B) * LW;
-          sg[e] = w << 31;
-        }
-        const float* arow = stage + rr * NC;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const uint32_t col = (uint32_t)(c + r) & (uint32_t)(NC - 1);
-          const uint32_t a = __float_as_uint(arow[col]);
-          if (bv[0]) red_shared_f32(ad[0] + 4u * col, __uint_as_float(a ^ sg[0]));
-          if (bv[1]) red_shared_f32(ad[1] + 4u * col, __uint_as_float(a ^ sg[1]));
-        }
+    // Stream output index of (row, pair) = row * kp + hp + 1; the next round's is RB * kp further on.
+    const uint64_t idx0 = (uint64_t)(r0 + box0 + r) * (uint64_t)kp + (uint64_t)hp + 1ull;
+    uint64_t z = D.seed + idx0 * kSplitMixGamma;
+    const uint64_t dz = (uint64_t)(RB * kp) * kSplitMixGamma;
+    if (full_lanes && nr_box == SB) {
+      for (int hb = 0; hb < D.mb; ++hb, z += dz)
+        lr_round<NC, false>(D, z, r, flip, stage + (hb * RB + r) * NC, base, bv, LW);
+    } else {
+      for (int hb = 0; hb < D.mb; ++hb, z += dz) {
+        const int rr = hb * RB + r;  // row of the box
+        if (r < RB && rr < nr_box) lr_round<NC, true>(D, z, r, flip, stage + rr * NC, base, bv, LW);
       }
     }
     __syncwarp();
