@@ -103,6 +103,31 @@ def test_atomic_mode_ragged_and_edges(sk, dev, rule, shape):
     assert oracle.rel_fro(_as64(got, rule), Y64) <= TOL[rule]
 
 
+# Small-integer data: every FP32 partial sum of a chunk is exact, so the atomic kernel's result does
+# not depend on its summation order and must equal the canonical order bit for bit. With k in
+# {1, 4, 16} the scale 1/sqrt(k) is a power of two and the per-chunk FP16 values and their sums in Y
+# stay exact too (several chunks); with k in {3, 8} the scaled chunk total is rounded once, so a
+# single chunk keeps Y order-independent (every rule, dither included). Any wrong target, sign or
+# column in the scatter changes an integer sum.
+# (n a multiple of 4 lets A go through TMA, the lane-row path; n = 13 takes the direct-load path.)
+@pytest.mark.parametrize("shape,R,rules", [
+    ((50001, 64, 4096, 8), 50016, RULES),        # the bench geometry (lane-row path, 8 columns per item)
+    ((50001, 12, 1024, 4), 0, [0, 1, 2]),        # several chunks, one partly filled 16-column tile
+    ((50001, 13, 1024, 4), 0, [0, 1, 2]),        # direct loads (row stride not a multiple of 16 bytes)
+    ((20000, 40, 4096, 16), 0, [0, 1, 2]),
+    ((30011, 20, 96, 3), 30016, RULES),          # odd k: the last pair has one block
+    ((40000, 36, 512, 1), 0, [0, 1, 2]),         # CountSketch
+])
+def test_atomic_mode_exact_on_integer_data(sk, dev, shape, R, rules):
+    m, n, d, k = shape
+    A = np.random.default_rng(m + k).integers(-3, 4, size=(m, n)).astype(np.float32)
+    for rule in rules:
+        params = {"chunk_rows": R} if R else {}
+        got, _, Rg = _apply(sk, A, d, k, rule, 1234 + k, dev, **params)
+        ref = oracle.sketch_canonical(A, d, k, 1234 + k, rule, Rg)
+        assert np.array_equal(got, ref), (rule, np.count_nonzero(got != ref))
+
+
 @pytest.mark.parametrize("rule", RULES)
 def test_lda_and_row_offset(sk, dev, rule):
     import torch
