@@ -41,6 +41,7 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "sweep_m4M_n64_d4096_k8"
 METRIC = "SA sketch HBM GB/s (% of peak) FP16 vs FP32 at equal distortion; p99 solve ms"
 KERNEL_SOURCES = ["paper_2606_20195_gb300/csrc/sk_tile.cuh", "paper_2606_20195_gb300/csrc/sk_kernels.cu",
+                  "paper_2606_20195_gb300/csrc/sk_own.cu",
                   "paper_2606_20195_gb300/csrc/sk_device.cuh"]
 
 
@@ -60,9 +61,9 @@ def measured_peaks() -> dict:
     return {}
 
 
-def traffic_record(workload: str, rule: str):
+def traffic_record(kernel: str, workload: str, rule: str):
     """DRAM traffic per launch from the committed ncu summary, if it was taken on these sources."""
-    p = os.path.join(HERE, "profiles", f"tile_kernel_{workload}_{rule}_traffic.txt")
+    p = os.path.join(HERE, "profiles", f"{kernel}_{workload}_{rule}_traffic.txt")
     if not os.path.exists(p):
         return None
     kv = {}
@@ -369,6 +370,8 @@ def main() -> int:
     clocks = clk.summary()
     launches_per_step = plan.get(sk.SK_PARAM_LAST_LAUNCHES)
     R_used = plan.get(sk.SK_PARAM_LAST_CHUNK_ROWS)
+    kernel_name = {sk.SK_KERNEL_TILE: "tile_kernel", sk.SK_KERNEL_OWNER: "own_kernel",
+                   sk.SK_KERNEL_LITERAL: "literal_kernel"}.get(plan.get(sk.SK_PARAM_LAST_KERNEL), "det_kernel")
     t = torch.tensor([total_ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -411,8 +414,8 @@ def main() -> int:
     avg_launch_ms = statistics.mean(per_ms)
     achieved = bytes_step / (avg_launch_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_record(args.workload, args.rule), "peak_source": peak_note,
-                "kernel": f"sk::tile_kernel<{args.rule}>",
+                "traffic": traffic_record(kernel_name, args.workload, args.rule), "peak_source": peak_note,
+                "kernel": f"sk::{kernel_name}<{args.rule}>",
                 "algorithmic_bytes_per_launch": bytes_step}
 
     extras = {}

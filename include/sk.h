@@ -72,8 +72,13 @@ typedef enum {
   /* Global index of the first row of A passed to sk_apply (for row-sharded matrices: S and the
    * chunk index depend on the global row). Default 0. */
   SK_PARAM_ROW_OFFSET = 3,
-  /* Kernel choice: SK_KERNEL_AUTO (default), SK_KERNEL_TILE (on-chip chunk accumulation),
-   * SK_KERNEL_LITERAL (one global atomic per element and nonzero, the paper's design; R must be 1). */
+  /* Kernel choice: SK_KERNEL_AUTO (default), SK_KERNEL_TILE (on-chip chunk accumulation with
+   * shared-memory atomics), SK_KERNEL_LITERAL (one global atomic per element and nonzero, the
+   * paper's design; R must be 1), SK_KERNEL_OWNER (on-chip chunk accumulation in which every
+   * accumulator row has one owning warp: no atomics; needs n >= 32, A 16-byte aligned with lda a
+   * multiple of 4, and B*128 bytes of shared memory per block; SK_ERR_UNSUPPORTED otherwise).
+   * Inside a work item the owner kernel adds rows in ascending order, so a chunk processed as one
+   * work item has exactly the canonical FP32 chunk total. AUTO takes the tile kernel. */
   SK_PARAM_KERNEL = 4,
   /* Columns per work item of the tile kernel (4, 8, 16 or 32; 0 = automatic). */
   SK_PARAM_TILE_COLS = 5,
@@ -85,11 +90,14 @@ typedef enum {
   SK_PARAM_LAST_CHUNK_ROWS = 8,
   /* Read-only: sticky status bits the sketch kernels of this plan set on the device (bit 0: a
    * bounded wait gave up, the results of that call are invalid). Reading it synchronizes the device. */
-  SK_PARAM_DEVICE_STATUS = 9
+  SK_PARAM_DEVICE_STATUS = 9,
+  /* Read-only: the kernel the last sketch ran: SK_KERNEL_TILE (1), SK_KERNEL_LITERAL (2),
+   * SK_KERNEL_OWNER (3), or 4 for the deterministic-mode kernel; 0 before the first sketch. */
+  SK_PARAM_LAST_KERNEL = 10
 } sk_param;
 
 enum { SK_MODE_ATOMIC = 0, SK_MODE_DETERMINISTIC = 1, SK_MODE_SERIAL_TILE = 2 };
-enum { SK_KERNEL_AUTO = 0, SK_KERNEL_TILE = 1, SK_KERNEL_LITERAL = 2 };
+enum { SK_KERNEL_AUTO = 0, SK_KERNEL_TILE = 1, SK_KERNEL_LITERAL = 2, SK_KERNEL_OWNER = 3 };
 
 typedef struct sk_plan_s* sk_plan;
 

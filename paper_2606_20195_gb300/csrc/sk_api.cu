@@ -49,6 +49,7 @@ struct sk_plan_s {
   int32_t tile_cols = 0;
   int32_t threads = 0;
   int64_t last_launches = 0, last_R = 0;
+  int32_t last_kernel = 0;  // kernel of the last sketch: 1 tile, 2 literal, 3 owner, 4 deterministic
   // device scratch
   float* det_P = nullptr;
   size_t det_P_bytes = 0;
@@ -101,6 +102,7 @@ struct TileCfg {
   int64_t R = 0;
   bool serial = false;
   bool lr = false;
+  bool own = false;
 };
 
 // Default chunk length: at most 8 chunks per matrix (each output then receives at most 8 rounded
@@ -110,7 +112,61 @@ int64_t default_chunk_rows(int64_t m) {
   return ((R + 31) / 32) * 32;
 }
 
-sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, TileCfg* cfg) {
+// Whether A (device pointer, row stride lda) can be staged through TMA: 16-byte-aligned base and a
+// row stride that is a multiple of 16 bytes.
+bool tma_layout_ok(const void* A, int64_t lda) {
+  return (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && (lda & 3) == 0;
+}
+
+// Split each chunk into slices until there are about 4 work items per resident CTA, keeping slices
+// at least max(4096, 2d) rows long so the partial flushes (d x NC floats each) stay small.
+int32_t choose_slices(const sk_plan_s* p, int64_t rows, int64_t R, int64_t ncg, int64_t nbg, int32_t cps,
+                      const DevInfo& di) {
+  const int64_t chunks = (rows + R - 1) / R + 1;
+  const int64_t target = 4 * (int64_t)di.sms * std::max(cps, 1);
+  const int64_t per_chunk = std::max<int64_t>(1, (target + chunks * ncg * nbg - 1) / (chunks * ncg * nbg));
+  const int64_t min_rows = std::max<int64_t>(4096, 2 * p->d);
+  const int64_t max_slices = std::max<int64_t>(1, std::min(R, rows) / min_rows);
+  return (int32_t)std::min<int64_t>(per_chunk, std::min<int64_t>(max_slices, 4096));
+}
+
+// Owner-kernel configuration (atomic mode, SK_KERNEL_OWNER): blocks per item kb = 2 when two blocks
+// of 32-column lines fit in shared memory, else 1; false if the kernel does not apply.
+bool choose_own(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, bool tma_ok, TileCfg* cfg) {
+  if (p->mode != SK_MODE_ATOMIC || !tma_ok || n < 32 || rows >= ((int64_t)1 << 31)) return false;
+  if (p->kernel != SK_KERNEL_OWNER) return false;
+  const size_t optin = (size_t)std::min(di.optin, 232448) - 1024;
+  int32_t kb = 0;
+  if (p->k >= 2 && own_smem_bytes(p->B, 2) <= optin) kb = 2;
+  else if (own_smem_bytes(p->B, 1) <= optin) kb = 1;
+  if (kb == 0) return false;
+  const int64_t R = p->R > 0 ? p->R : default_chunk_rows(p->m);
+  const int32_t cps = own_ctas_per_sm(p->rule, own_smem_bytes(p->B, kb));
+  if (cps < 1) return false;
+  const int64_t ncg = (n + 31) / 32;
+  const int64_t nbg = (p->k + kb - 1) / kb;
+  cfg->NC = 32;
+  cfg->kb = kb;
+  cfg->threads = own_threads();
+  cfg->grid = 0;
+  cfg->R = R;
+  cfg->slices = choose_slices(p, rows, R, ncg, nbg, cps, di);
+  cfg->depth = 1;
+  cfg->mb = 1;
+  cfg->serial = false;
+  cfg->lr = false;
+  cfg->own = true;
+  return true;
+}
+
+sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, TileCfg* cfg,
+                      bool tma_ok = false) {
+  if (choose_own(p, n, rows, di, tma_ok, cfg)) return SK_OK;
+  if (p->kernel == SK_KERNEL_OWNER)
+    return set_error(SK_ERR_UNSUPPORTED,
+                     "owner kernel: needs atomic mode, n >= 32, A 16-byte aligned with lda %% 4 == 0 and "
+                     "2 x %lld x 128 bytes of shared memory",
+                     (long long)p->B);
   const bool serial = (p->mode == SK_MODE_SERIAL_TILE);
   const int32_t threads = serial ? 32 : (p->threads > 0 ? p->threads : 1024);
   const int32_t nwarps = threads / 32;
@@ -158,17 +214,10 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
   int64_t R = p->R > 0 ? p->R : default_chunk_rows(p->m);
   int32_t slices = 1;
   if (!serial) {
-    // Split chunks into slices until there are ~4 work items per resident CTA, keeping slices at
-    // least max(4096, 2d) rows long so the partial flush (d x NC floats) stays small.
     const int64_t ncg = (n + NC - 1) / NC;
     const int64_t nbg = (p->k + kb - 1) / kb;
-    const int64_t chunks = (rows + R - 1) / R + 1;
     const int32_t cps = tile_ctas_per_sm(p->rule, threads, tile_smem_bytes(p->B, kb, NC, threads, p->k, depth, mb));
-    const int64_t target = 4 * (int64_t)di.sms * std::max(cps, 1);
-    const int64_t per_chunk = std::max<int64_t>(1, (target + chunks * ncg * nbg - 1) / (chunks * ncg * nbg));
-    const int64_t min_rows = std::max<int64_t>(4096, 2 * p->d);
-    const int64_t max_slices = std::max<int64_t>(1, std::min(R, rows) / min_rows);
-    slices = (int32_t)std::min<int64_t>(per_chunk, std::min<int64_t>(max_slices, 4096));
+    slices = choose_slices(p, rows, R, ncg, nbg, cps, di);
   }
   cfg->NC = NC;
   cfg->kb = kb;
@@ -179,6 +228,7 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
   cfg->depth = depth;
   cfg->mb = mb;
   cfg->lr = lr;
+  cfg->own = false;
   cfg->serial = serial;
   return SK_OK;
 }
@@ -241,6 +291,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
     L.col_off = col_off;
     cudaError_t e = launch_det(L, st, launches);
     if (e != cudaSuccess) return cuda_fail(e, "deterministic kernel launch");
+    p->last_kernel = 4;
     if (R_used) *R_used = R;
     return SK_OK;
   }
@@ -261,11 +312,12 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
     L.col_off = col_off;
     cudaError_t e = launch_literal(L, st, launches);
     if (e != cudaSuccess) return cuda_fail(e, "literal kernel launch");
+    p->last_kernel = SK_KERNEL_LITERAL;
     if (R_used) *R_used = 1;
     return SK_OK;
   }
   TileCfg cfg;
-  s = choose_tile(p, n, rows, di, &cfg);
+  s = choose_tile(p, n, rows, di, &cfg, tma_layout_ok(A, lda));
   if (s != SK_OK) return s;
   if (R_fixed > 0) cfg.R = R_fixed;
   TileLaunch L;
@@ -289,6 +341,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
   L.depth = cfg.depth;
   L.mb = cfg.mb;
   L.lr = cfg.lr ? 1 : 0;
+  L.own = cfg.own ? 1 : 0;
   L.col_off = col_off;
   L.allow_tma = 1;
   if (!p->dstatus) {
@@ -336,7 +389,8 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
     L.counters = p->counters;
   }
   cudaError_t e = launch_tile(L, st, launches);
-  if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");
+  if (e != cudaSuccess) return cuda_fail(e, cfg.own ? "owner kernel launch" : "tile kernel launch");
+  p->last_kernel = cfg.own ? SK_KERNEL_OWNER : SK_KERNEL_TILE;
   if (R_used) *R_used = cfg.R;
   return SK_OK;
 }
@@ -389,7 +443,7 @@ sk_status sk_plan_set(sk_plan p, int32_t key, int64_t v) {
       p->row_offset = v;
       return SK_OK;
     case SK_PARAM_KERNEL:
-      if (v < SK_KERNEL_AUTO || v > SK_KERNEL_LITERAL) return set_error(SK_ERR_INVALID_ARG, "unknown kernel %lld", (long long)v);
+      if (v < SK_KERNEL_AUTO || v > SK_KERNEL_OWNER) return set_error(SK_ERR_INVALID_ARG, "unknown kernel %lld", (long long)v);
       p->kernel = (int32_t)v;
       return SK_OK;
     case SK_PARAM_TILE_COLS:
@@ -419,6 +473,7 @@ sk_status sk_plan_get(sk_plan p, int32_t key, int64_t* v) {
     case SK_PARAM_THREADS: *v = p->threads; return SK_OK;
     case SK_PARAM_LAST_LAUNCHES: *v = p->last_launches; return SK_OK;
     case SK_PARAM_LAST_CHUNK_ROWS: *v = p->last_R; return SK_OK;
+    case SK_PARAM_LAST_KERNEL: *v = p->last_kernel; return SK_OK;
     case SK_PARAM_DEVICE_STATUS: {
       *v = 0;
       if (!p->dstatus) return SK_OK;
@@ -704,7 +759,7 @@ sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, i
   s = dev_info(&di);
   if (s != SK_OK) return s;
   TileCfg cfg;
-  s = choose_tile(p, n, p->m, di, &cfg);
+  s = choose_tile(p, n, p->m, di, &cfg, tma_layout_ok(A, lda));
   if (s != SK_OK) return s;
   L->A = A;
   L->Y = Y;
@@ -726,6 +781,7 @@ sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, i
   L->depth = cfg.depth;
   L->mb = cfg.mb;
   L->lr = cfg.lr ? 1 : 0;
+  L->own = cfg.own ? 1 : 0;
   L->col_off = 0;
   L->allow_tma = 1;
   L->status = nullptr;
@@ -736,9 +792,10 @@ sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, i
 
 size_t noalloc_elem_size(const sk_plan_s* p) { return elem_size(p->rule); }
 
-void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R) {
+void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R, bool own) {
   p->last_launches = launches;
   p->last_R = R;
+  p->last_kernel = own ? SK_KERNEL_OWNER : SK_KERNEL_TILE;
 }
 
 }  // namespace sk

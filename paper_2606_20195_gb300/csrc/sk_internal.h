@@ -28,6 +28,7 @@ struct TileLaunch {
   int32_t depth;      // TMA ring slots per warp (1..4)
   int32_t mb;         // hash rounds per TMA box (1, or more when every work item takes the fast path)
   int32_t lr = 0;     // 1: lane-row scatter (one block group; used only when A is staged through TMA)
+  int32_t own = 0;    // 1: owner kernel (NC = 32, kb = 1 or 2 blocks per item, A through TMA)
 };
 
 // Shared-memory bytes the tile kernel needs for (B, kb, NC, threads, k, ring depth, rounds per box).
@@ -38,6 +39,12 @@ bool encode_a_map(void* map, const float* A, int64_t lda, int64_t n, int64_t row
 int32_t tile_slots(int32_t NC, int32_t kb);
 // Enqueue the chunked tile kernel (atomic flush). Returns a CUDA error code.
 cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches);
+// Owner kernel (sk_own.cu): shared-memory bytes for kb blocks of B rows, threads per CTA, resident
+// CTAs per SM, and the launch (L.NC == 32, L.kb in {1, 2}; fails if A cannot go through TMA).
+size_t own_smem_bytes(int64_t B, int32_t kb);
+int32_t own_threads();
+int32_t own_ctas_per_sm(int32_t rule, size_t smem);
+cudaError_t launch_own(const TileLaunch& L, cudaStream_t st, int32_t* launches);
 // Chunks, column groups and block groups of a launch.
 void tile_geometry(const TileLaunch& L, int64_t* chunks, int32_t* ncg, int32_t* nbg);
 // Resident CTAs per SM of the tile kernel for (rule, threads, dynamic shared memory).

@@ -14,20 +14,6 @@
 namespace sk {
 
 // ------------------------------------------------------------------ tile kernel
-struct TileGrid {
-  TileDesc D;
-  int64_t row_begin, row_end;  // global rows processed
-  int64_t R;                   // chunk rows
-  int64_t t_first;             // first chunk index
-  int64_t items;               // chunks * slices * nbg * ncg
-  int32_t ncg, nbg, slices;
-  int32_t acc_floats;          // floats of the accumulator (multiple of 4)
-  float* P;                    // slices > 1: per-chunk FP32 totals, chunk-major, d x n each (zero)
-  int32_t* counters;           // slices > 1: finished slices per (chunk, bg, g) (zero)
-  unsigned* status;            // sticky status word (kStatus*), may be null
-  int32_t use_tma;             // 1: A arrives through the tensor map
-  int32_t depth;               // TMA ring slots per warp
-};
 
 template <int RULE>
 __global__ void __launch_bounds__(1024) tile_kernel(const TileGrid P, const __grid_constant__ CUtensorMap tmap) {
@@ -146,6 +132,7 @@ void tile_geometry(const TileLaunch& L, int64_t* chunks, int32_t* ncg, int32_t* 
 }
 
 cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches) {
+  if (L.own) return launch_own(L, st, launches);
   TileGrid P;
   const int64_t B = L.d / L.k;
   P.D.A = L.A;

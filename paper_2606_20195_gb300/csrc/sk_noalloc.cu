@@ -12,7 +12,7 @@
 namespace sk {
 sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, int64_t n, void* Y, TileLaunch* L);
 size_t noalloc_elem_size(const sk_plan_s* p);
-void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R);
+void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R, bool own);
 }  // namespace sk
 
 using namespace sk;
@@ -81,6 +81,6 @@ extern "C" SK_API sk_status sk_apply_noalloc(sk_plan p, const float* A, int64_t 
   int32_t launches = 0;
   e = launch_tile(L, st, &launches);
   if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "tile kernel launch: %s", cudaGetErrorString(e));
-  noalloc_record(p, launches, L.R);
+  noalloc_record(p, launches, L.R, L.own != 0);
   return SK_OK;
 }

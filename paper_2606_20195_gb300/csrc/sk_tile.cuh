@@ -45,6 +45,22 @@ struct TileDesc {
   int32_t lr;       // 1: every work item holds all k blocks and takes the lane-row TMA path
 };
 
+// Launch parameters of the chunked kernels (tile kernel and owner kernel).
+struct TileGrid {
+  TileDesc D;
+  int64_t row_begin, row_end;  // global rows processed
+  int64_t R;                   // chunk rows
+  int64_t t_first;             // first chunk index
+  int64_t items;               // chunks * slices * nbg * ncg
+  int32_t ncg, nbg, slices;
+  int32_t acc_floats;          // floats of the accumulator (multiple of 4)
+  float* P;                    // slices > 1: per-chunk FP32 totals, chunk-major, d x n each (zero)
+  int32_t* counters;           // slices > 1: finished slices per (chunk, bg, g) (zero)
+  unsigned* status;            // sticky status word (kStatus*), may be null
+  int32_t use_tma;             // 1: A arrives through the tensor map
+  int32_t depth;               // TMA ring slots per warp
+};
+
 // Per-warp TMA staging ring: `depth` slots of RB x NC floats (128-byte aligned) and their mbarriers.
 // `uses` counts the batches this warp has consumed so far; slot and phase parity derive from it.
 struct WarpRing {

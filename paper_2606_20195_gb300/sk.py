@@ -17,9 +17,9 @@ SK_FP32, SK_FP16_RN, SK_FP16_SR, SK_FP16_DITHER = range(4)
 RULES = {"fp32": SK_FP32, "fp16_rn": SK_FP16_RN, "fp16_sr": SK_FP16_SR, "fp16_dither": SK_FP16_DITHER}
 SK_PARAM_CHUNK_ROWS, SK_PARAM_MODE, SK_PARAM_ROW_OFFSET, SK_PARAM_KERNEL = 1, 2, 3, 4
 SK_PARAM_TILE_COLS, SK_PARAM_THREADS, SK_PARAM_LAST_LAUNCHES, SK_PARAM_LAST_CHUNK_ROWS = 5, 6, 7, 8
-SK_PARAM_DEVICE_STATUS = 9
+SK_PARAM_DEVICE_STATUS, SK_PARAM_LAST_KERNEL = 9, 10
 SK_MODE_ATOMIC, SK_MODE_DETERMINISTIC, SK_MODE_SERIAL_TILE = 0, 1, 2
-SK_KERNEL_AUTO, SK_KERNEL_TILE, SK_KERNEL_LITERAL = 0, 1, 2
+SK_KERNEL_AUTO, SK_KERNEL_TILE, SK_KERNEL_LITERAL, SK_KERNEL_OWNER = 0, 1, 2, 3
 
 # Every symbol include/sk.h declares.
 EXPORTS = [

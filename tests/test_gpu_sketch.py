@@ -109,7 +109,8 @@ def test_atomic_mode_ragged_and_edges(sk, dev, rule, shape):
 # stay exact too (several chunks); with k in {3, 8} the scaled chunk total is rounded once, so a
 # single chunk keeps Y order-independent (every rule, dither included). Any wrong target, sign or
 # column in the scatter changes an integer sum.
-# (n a multiple of 4 lets A go through TMA, the lane-row path; n = 13 takes the direct-load path.)
+# (n a multiple of 4 lets A go through TMA and the tile kernel take the lane-row path; n = 13 takes
+# the direct-load path. The owner kernel runs the same cases where it applies, n >= 32.)
 @pytest.mark.parametrize("shape,R,rules", [
     ((50001, 64, 4096, 8), 50016, RULES),        # the bench geometry (lane-row path, 8 columns per item)
     ((50001, 12, 1024, 4), 0, [0, 1, 2]),        # several chunks, one partly filled 16-column tile
@@ -118,11 +119,15 @@ def test_atomic_mode_ragged_and_edges(sk, dev, rule, shape):
     ((30011, 20, 96, 3), 30016, RULES),          # odd k: the last pair has one block
     ((40000, 36, 512, 1), 0, [0, 1, 2]),         # CountSketch
 ])
-def test_atomic_mode_exact_on_integer_data(sk, dev, shape, R, rules):
+@pytest.mark.parametrize("kernel", ["tile", "owner"])
+def test_atomic_mode_exact_on_integer_data(sk, dev, shape, R, rules, kernel):
     m, n, d, k = shape
+    if kernel == "owner" and n < 32:
+        pytest.skip("the owner kernel needs n >= 32")
     A = np.random.default_rng(m + k).integers(-3, 4, size=(m, n)).astype(np.float32)
     for rule in rules:
         params = {"chunk_rows": R} if R else {}
+        params["kernel"] = sk.SK_KERNEL_TILE if kernel == "tile" else sk.SK_KERNEL_OWNER
         got, _, Rg = _apply(sk, A, d, k, rule, 1234 + k, dev, **params)
         ref = oracle.sketch_canonical(A, d, k, 1234 + k, rule, Rg)
         assert np.array_equal(got, ref), (rule, np.count_nonzero(got != ref))
