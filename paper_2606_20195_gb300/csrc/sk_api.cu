@@ -103,6 +103,7 @@ struct TileCfg {
   bool serial = false;
   bool lr = false;
   bool own = false;
+  bool vec = false;
 };
 
 // Default chunk length: at most 8 chunks per matrix (each output then receives at most 8 rounded
@@ -156,6 +157,7 @@ bool choose_own(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, 
   cfg->serial = false;
   cfg->lr = false;
   cfg->own = true;
+  cfg->vec = false;
   return true;
 }
 
@@ -168,6 +170,36 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
                      "2 x %lld x 128 bytes of shared memory",
                      (long long)p->B);
   const bool serial = (p->mode == SK_MODE_SERIAL_TILE);
+  if (n == 1 && !serial && p->tile_cols <= 4) {
+    // A single column: the vector path (one thread per row, accumulator lines of one quad).
+    const int32_t threads = p->threads > 0 ? p->threads : 1024;
+    int32_t kb = 0;
+    for (int32_t kbt = p->k; kbt >= 1; --kbt) {
+      const int64_t fl = tile_acc_floats((uint32_t)p->B, kbt, tile_slots(4, kbt), 4);
+      if (tile_smem_bytes(p->B, kbt, 4, threads, p->k, 1) <= (size_t)std::min(di.optin, 232448) - 1024 && fl < (1 << 29)) {
+        kb = kbt;
+        break;
+      }
+    }
+    if (kb > 0) {
+      const int64_t R = p->R > 0 ? p->R : default_chunk_rows(p->m);
+      const int64_t nbg = (p->k + kb - 1) / kb;
+      const int32_t cps = tile_ctas_per_sm(p->rule, threads, tile_smem_bytes(p->B, kb, 4, threads, p->k, 1));
+      cfg->NC = 4;
+      cfg->kb = kb;
+      cfg->threads = threads;
+      cfg->grid = 0;
+      cfg->R = R;
+      cfg->slices = choose_slices(p, rows, R, 1, nbg, cps, di);
+      cfg->depth = 1;
+      cfg->mb = 1;
+      cfg->serial = false;
+      cfg->lr = false;
+      cfg->own = false;
+      cfg->vec = true;
+      return SK_OK;
+    }
+  }
   const int32_t threads = serial ? 32 : (p->threads > 0 ? p->threads : 1024);
   const int32_t nwarps = threads / 32;
   const int32_t RB = 32 / ((p->k + 1) / 2);
@@ -229,6 +261,7 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
   cfg->mb = mb;
   cfg->lr = lr;
   cfg->own = false;
+  cfg->vec = false;
   cfg->serial = serial;
   return SK_OK;
 }
@@ -342,8 +375,9 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
   L.mb = cfg.mb;
   L.lr = cfg.lr ? 1 : 0;
   L.own = cfg.own ? 1 : 0;
+  L.vec = cfg.vec ? 1 : 0;
   L.col_off = col_off;
-  L.allow_tma = 1;
+  L.allow_tma = cfg.vec ? 0 : 1;
   if (!p->dstatus) {
     if (cudaMalloc(&p->dstatus, sizeof(unsigned)) != cudaSuccess) {
       cudaGetLastError();
@@ -782,6 +816,7 @@ sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, i
   L->mb = cfg.mb;
   L->lr = cfg.lr ? 1 : 0;
   L->own = cfg.own ? 1 : 0;
+  L->vec = cfg.vec ? 1 : 0;
   L->col_off = 0;
   L->allow_tma = 1;
   L->status = nullptr;

@@ -237,6 +237,7 @@ sk_status build_batch(sk_batch_s* b) {
     D.D.tmap = nullptr;  // set after the maps are uploaded
     D.D.mb = 1;
     D.D.lr = 0;
+    D.D.vec = 0;
     ncgs[i] = (int32_t)((it.n + NC - 1) / NC);
     nbgs[i] = (it.k + kb - 1) / kb;
     max_floats = std::max(max_floats, (size_t)tile_acc_floats((uint32_t)B, kb, D.D.S, NC));

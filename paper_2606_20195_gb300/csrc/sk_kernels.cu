@@ -169,6 +169,11 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   P.D.mb = std::max(1, L.mb);
   P.use_tma = (L.allow_tma && encode_a_map(&tmap, L.A, L.lda, L.n, L.row_end - L.row_begin, L.NC, RB * P.D.mb)) ? 1 : 0;
   P.D.lr = (P.use_tma && L.lr && L.kb == L.k) ? 1 : 0;
+  P.D.vec = (L.vec && L.n == 1 && L.NC == 4) ? 1 : 0;
+  if (P.D.vec) {
+    P.use_tma = 0;
+    P.D.lr = 0;
+  }
   P.depth = std::max(1, L.depth);
   const size_t smem = tile_smem_bytes(B, L.kb, L.NC, L.threads, L.k, P.depth, P.D.mb);
   int dev = 0;

@@ -270,6 +270,7 @@ cudaError_t launch_own(const TileLaunch& L, cudaStream_t st, int32_t* launches) 
   P.D.tmap = nullptr;
   P.D.mb = 1;
   P.D.lr = 0;
+  P.D.vec = 0;
   P.row_begin = L.row_begin;
   P.row_end = L.row_end;
   P.R = L.R;

@@ -43,6 +43,7 @@ struct TileDesc {
   const void* tmap; // 2-D tensor map over A (box NC x RB*mb), or null: direct loads
   int32_t mb;       // hash rounds (of RB = 32/kp rows) per TMA box
   int32_t lr;       // 1: every work item holds all k blocks and takes the lane-row TMA path
+  int32_t vec;      // 1: n = 1, one thread per row (tile_scatter_vec)
 };
 
 // Launch parameters of the chunked kernels (tile kernel and owner kernel).
@@ -381,7 +382,7 @@ __device__ __forceinline__ void red_shared_f32(uint32_t addr, float v) {
 // every lane holds a row and both its blocks exist.
 // `z` is the SplitMix64 state of the lane's stream output (seed + index * golden gamma).
 template <int NC, bool PRED>
-__device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int r, int flip, const float* arow,
+__device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int rot, int flip, const float* arow,
                                          const uint32_t base[2], const bool bv[2], uint32_t LW) {
   const uint64_t h = splitmix_finalize(z);
   uint32_t ad[2], sg[2];
@@ -394,7 +395,7 @@ __device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int r, i
   // (a partial unroll at NC = 32 keeps the loads in flight within the register budget)
 #pragma unroll(NC > 16 ? 8 : NC)
   for (int c = 0; c < NC; ++c) {
-    const uint32_t col = (uint32_t)(c + r) & (uint32_t)(NC - 1);
+    const uint32_t col = (uint32_t)(c + rot) & (uint32_t)(NC - 1);
     const uint32_t a = __float_as_uint(arow[col]);
     if (!PRED || bv[0]) red_shared_f32(ad[0] + 4u * col, __uint_as_float(a ^ sg[0]));
     if (!PRED || bv[1]) red_shared_f32(ad[1] + 4u * col, __uint_as_float(a ^ sg[1]));
@@ -404,11 +405,13 @@ __device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int r, i
 // Lane-row TMA path, for work items that hold all k blocks (j0 = 0, kbe = k). Within a hash round of
 // RB = 32/kp rows, lane (r, hp) owns row r and the pair of blocks (2hp, 2hp+1): it computes that
 // pair's 64-bit stream output, keeps both targets and signs in registers and adds its row's NC values
-// into both targets, column (c + r) mod NC at step c. A lane-dependent flip decides which block of the
-// pair comes first. With S*NC = 32 floats per line, the 32 lanes of one access then differ in
-// (slot mod S, column) and hit 32 distinct banks whenever kp = S and RB <= NC (k = 8 with NC = 8,
-// for example); other shapes stay correct with some bank conflicts. No per-update target word is
-// read from shared memory and no warp-level exchange is needed, so a round is straight-line code.
+// into both targets, column (c + rot) mod NC at step c with rot = r + RB * floor(hp / S). A
+// lane-dependent flip decides which block of the pair comes first, so that at a given step lane
+// (r, hp) writes slot (2hp + flip) mod S. With S*NC = 32 floats per line and kp >= S, the lanes that
+// share a slot are the RB*kp/S = NC lanes (r, hp') with hp' = hp mod S, and rot takes NC distinct
+// values over them: the 32 lanes of one access hit 32 distinct banks (k = 8 with NC = 8 or 16, for
+// example); other shapes stay correct with some bank conflicts. No per-update target word is read
+// from shared memory and no warp-level exchange is needed, so a round is straight-line code.
 // Boxes, ring and bounded waits are as in tile_scatter_tma. Columns past n read TMA zero fill and
 // add zeros into accumulator columns that are never flushed.
 template <int NC>
@@ -424,6 +427,7 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
   const int r = lane / kp;
   const int hp = lane - r * kp;
   const int flip = ((2 * hp) / S + r / NC) & 1;
+  const int rot = r + RB * (hp / S);
   const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
   uint32_t base[2];
   bool bv[2];
@@ -475,11 +479,11 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
     const uint64_t dz = (uint64_t)(RB * kp) * kSplitMixGamma;
     if (full_lanes && nr_box == SB) {
       for (int hb = 0; hb < D.mb; ++hb, z += dz)
-        lr_round<NC, false>(D, z, r, flip, stage + (hb * RB + r) * NC, base, bv, LW);
+        lr_round<NC, false>(D, z, rot, flip, stage + (hb * RB + r) * NC, base, bv, LW);
     } else {
       for (int hb = 0; hb < D.mb; ++hb, z += dz) {
         const int rr = hb * RB + r;  // row of the box
-        if (r < RB && rr < nr_box) lr_round<NC, true>(D, z, r, flip, stage + rr * NC, base, bv, LW);
+        if (r < RB && rr < nr_box) lr_round<NC, true>(D, z, rot, flip, stage + rr * NC, base, bv, LW);
       }
     }
     __syncwarp();
@@ -496,11 +500,38 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
   return ok;
 }
 
-// Dispatch: the lane-row path when the host set it up, else on the passes per row of the work item
-// (blocks per lane group) for the unrolled path.
+// Vector path (n = 1): the accumulator is one FP32 value per target row, acc[jl*B + s], so the lanes
+// of an access spread over the banks with their (pseudo-random) targets. Each thread takes rows
+// r0 + tid, r0 + tid + blockDim, ... of the work item, loads the row's value (consecutive threads
+// read consecutive rows), evaluates the row's stream outputs for blocks j0 .. j0+kbe-1 and adds the
+// signed value into each block's target. Rows whose value is zero add nothing and are skipped.
+__device__ __forceinline__ void tile_scatter_vec(const TileDesc& D, int64_t r0, int64_t r1, int32_t j0, int32_t kbe,
+                                                 float* acc) {
+  const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const uint32_t a = __float_as_uint(__ldg(D.A + (i - D.row_base) * D.lda));
+    if ((a << 1) == 0u) continue;
+    uint64_t h = 0;
+    for (int jl = 0; jl < kbe; ++jl) {
+      const int j = j0 + jl;
+      if (jl == 0 || (j & 1) == 0) h = row_pair_bits(D.seed, (uint64_t)i, D.kp, (uint32_t)j >> 1);
+      const uint32_t w = block_word(h, (uint32_t)j);
+      const uint32_t line = (uint32_t)jl * D.B + word_to_slot(w, D.B);
+      red_shared_f32(acc_s + 4u * line, __uint_as_float(a ^ (w << 31)));
+    }
+  }
+}
+
+// Dispatch: the vector or lane-row path when the host set it up, else on the passes per row of the
+// work item (blocks per lane group) for the unrolled path.
 __device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
                                              int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
                                              int nwarps) {
+  if (D.vec) {
+    if (D.n != 1 || D.log2NC != 2) return false;
+    tile_scatter_vec(D, r0, r1, j0, kbe, acc);
+    return true;
+  }
   if (D.lr) {
     // Set up by the host only for one block group with a tensor map; refuse anything else, since its
     // boxes would not match what the host encoded.
@@ -614,6 +645,16 @@ __device__ __forceinline__ QuadIter quad_iter(const TileDesc& D) {
 template <int RULE>
 __device__ __forceinline__ void tile_flush(const TileDesc& D, int64_t t, int32_t g, int32_t j0, int32_t kbe,
                                            float* acc) {
+  if (D.vec) {
+    // one value per target row (n = 1)
+    for (int64_t f = threadIdx.x; f < (int64_t)kbe * D.B; f += blockDim.x) {
+      const float v = acc[f];
+      if (v == 0.f) continue;
+      acc[f] = 0.f;
+      emit_quad<RULE>(D, (uint32_t)j0 * D.B + (uint32_t)f, 0, make_float4(v, 0.f, 0.f, 0.f), t);
+    }
+    return;
+  }
   const QuadIter it = quad_iter(D);
   const int64_t total = (int64_t)kbe * D.B * it.nq;
   for (int64_t f = threadIdx.x; f < total; f += blockDim.x) {
@@ -633,6 +674,15 @@ __device__ __forceinline__ void tile_flush(const TileDesc& D, int64_t t, int32_t
 // zero the accumulator.
 __device__ __forceinline__ void tile_flush_partial(const TileDesc& D, int32_t g, int32_t j0, int32_t kbe, float* acc,
                                                    float* P) {
+  if (D.vec) {
+    for (int64_t f = threadIdx.x; f < (int64_t)kbe * D.B; f += blockDim.x) {
+      const float v = acc[f];
+      if (v == 0.f) continue;
+      acc[f] = 0.f;
+      atomicAdd(P + ((int64_t)j0 * D.B + f) * D.n, v);
+    }
+    return;
+  }
   const QuadIter it = quad_iter(D);
   const int64_t total = (int64_t)kbe * D.B * it.nq;
   const int64_t n = D.n;

@@ -118,6 +118,8 @@ def test_atomic_mode_ragged_and_edges(sk, dev, rule, shape):
     ((20000, 40, 4096, 16), 0, [0, 1, 2]),
     ((30011, 20, 96, 3), 30016, RULES),          # odd k: the last pair has one block
     ((40000, 36, 512, 1), 0, [0, 1, 2]),         # CountSketch
+    ((50001, 1, 1024, 4), 0, [0, 1, 2]),         # one column: the vector path
+    ((30011, 1, 96, 3), 30016, RULES),
 ])
 @pytest.mark.parametrize("kernel", ["tile", "owner"])
 def test_atomic_mode_exact_on_integer_data(sk, dev, shape, R, rules, kernel):
