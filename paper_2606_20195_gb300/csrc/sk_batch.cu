@@ -216,7 +216,10 @@ sk_status build_batch(sk_batch_s* b) {
     if (kb == 0)
       return set_error(SK_ERR_UNSUPPORTED, "batch item %d: a block of %lld rows does not fit in shared memory", i,
                        (long long)B);
-    slot_max = std::max(slot_max, ring_slot_bytes(RB, NC));
+    // One block group: the lane-row path with boxes of several hash rounds (up to 1 KiB), if A's
+    // layout allows TMA (decided below, when the maps are encoded).
+    const int32_t mb = (kb == it.k) ? std::max(1, std::min(8, 1024 / (RB * NC * 4))) : 1;
+    slot_max = std::max(slot_max, ring_slot_bytes(RB * mb, NC));
     BatchDesc& D = descs[i];
     D.D.A = it.A_dev;
     D.D.Y = it.Y_dev;
@@ -235,8 +238,8 @@ sk_status build_batch(sk_batch_s* b) {
     D.D.kb = kb;
     D.D.col_off = 0;
     D.D.tmap = nullptr;  // set after the maps are uploaded
-    D.D.mb = 1;
-    D.D.lr = 0;
+    D.D.mb = mb;
+    D.D.lr = (kb == it.k) ? 1 : 0;
     D.D.vec = 0;
     ncgs[i] = (int32_t)((it.n + NC - 1) / NC);
     nbgs[i] = (it.k + kb - 1) / kb;
@@ -298,9 +301,14 @@ sk_status build_batch(sk_batch_s* b) {
     memset(&maps[i], 0, sizeof(CUtensorMap));
     const sk_batch_item& it = b->items[i];
     has_map[i] = encode_a_map(&maps[i], it.A_dev, it.lda, it.n, it.m, 1 << descs[i].D.log2NC,
-                              32 / ((it.k + 1) / 2))
+                              (32 / ((it.k + 1) / 2)) * descs[i].D.mb)
                      ? 1
                      : 0;
+    if (!has_map[i]) {
+      // direct loads: the target-word path, one hash round per batch
+      descs[i].D.mb = 1;
+      descs[i].D.lr = 0;
+    }
   }
   if (cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * count) != cudaSuccess ||
       cudaMalloc(&b->d_status, sizeof(unsigned)) != cudaSuccess) {
