@@ -3,7 +3,8 @@
 Workload (default): the single-matrix sweep configuration m = 2^22, n = 64, d = 4096, k = 8,
 A FP32 iid N(0, 1) (the incoherent family), accumulation FP16 round-to-nearest (the headline rule);
 FP32 / stochastic / dithered variants are timed beside it. A is 1 GiB, larger than the 129 MB L2,
-so no L2 flush is needed between steps. One step = one sk_apply (zero Y, one tile-kernel launch).
+so no L2 flush is needed between steps. One step = one sk_apply (zero Y, the tile kernel, and the
+chunk-finish kernel when chunks are split into slices).
 
   value      device throughput, GB/s of (A read + Y written) with A resident in HBM
   e2e        the same metric through sk_apply_host with pinned host buffers (H2D of A and D2H of

@@ -210,10 +210,10 @@ SK_API void sk_batch_destroy(sk_batch batch);
  * memory is budgeted up front, an embedding application that owns all device memory). The paper has
  * no counterpart; this is an interface variant of the sketch call.
  *
- * Instead of plan-owned scratch, the kernel's scratch (per-chunk FP32 totals, slice counters and the
- * status word) lives in one fixed static device array of 16 MiB in this library. The caller still
- * passes A and Y exactly as for sk_apply. The call allocates nothing: no cudaMalloc, cudaFree or
- * allocating library routine; it only enqueues memsets and the kernel on `stream`.
+ * Instead of plan-owned scratch, the kernels' scratch (per-chunk FP32 totals and the status word)
+ * lives in one fixed static device array of 16 MiB in this library. The caller still passes A and Y
+ * exactly as for sk_apply. The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine; it only enqueues memsets and the kernels on `stream` (the same launches as sk_apply).
  *   - The first call on each device looks up the device address of that array
  *     (cudaGetSymbolAddress) with the device current; make that first call before any stream
  *     capture on the device.
@@ -221,7 +221,7 @@ SK_API void sk_batch_destroy(sk_batch batch);
  *     are rejected with SK_ERR_UNSUPPORTED and a message; use sk_apply for those.
  *   - Every call on a device shares the one array: calls that overlap on the GPU (different streams,
  *     or different host threads) race and give wrong results. Serialize them on one stream.
- *   - Only SK_MODE_ATOMIC with the tile kernel is supported (SK_ERR_UNSUPPORTED otherwise).
+ *   - Only SK_MODE_ATOMIC with the tile or owner kernel is supported (SK_ERR_UNSUPPORTED otherwise).
  */
 SK_API sk_status sk_apply_noalloc(sk_plan plan, const float* A_dev, int64_t lda, int64_t n, void* Y_dev, void* stream);
 

@@ -56,8 +56,6 @@ struct sk_plan_s {
   unsigned* dstatus = nullptr;  // sticky device status word of the sketch kernels
   float* tileP = nullptr;       // two-level chunk totals (zero between launches)
   size_t tileP_bytes = 0;
-  int32_t* counters = nullptr;  // slice counters (zero between launches)
-  size_t counters_bytes = 0;
   void* solve_buf = nullptr;
   size_t solve_bytes = 0;
   size_t solve_status_off = 0, solve_kappa_off = 0;
@@ -119,16 +117,31 @@ bool tma_layout_ok(const void* A, int64_t lda) {
   return (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && (lda & 3) == 0;
 }
 
-// Split each chunk into slices until there are about 4 work items per resident CTA, keeping slices
-// at least max(4096, 2d) rows long so the partial flushes (d x NC floats each) stay small.
+// Split each chunk into slices: at least about 4 work items per resident CTA, slices at least
+// max(4096, 2d) rows long so the partial flushes (d x NC floats each) stay small, and, among the
+// slice counts up to 4x that minimum, the one whose work items fill the last round of CTAs best
+// (the items of one launch are of equal size, so a last round of 120 items on 152 CTAs idles 21 % of
+// the GPU for a whole item).
 int32_t choose_slices(const sk_plan_s* p, int64_t rows, int64_t R, int64_t ncg, int64_t nbg, int32_t cps,
                       const DevInfo& di) {
-  const int64_t chunks = (rows + R - 1) / R + 1;
-  const int64_t target = 4 * (int64_t)di.sms * std::max(cps, 1);
-  const int64_t per_chunk = std::max<int64_t>(1, (target + chunks * ncg * nbg - 1) / (chunks * ncg * nbg));
+  const int64_t first = ((p->row_offset % R) + R) % R;  // offset of the first row inside its chunk
+  const int64_t chunks = (first + rows + R - 1) / R;
+  const int64_t G = (int64_t)di.sms * std::max(cps, 1);
+  const int64_t per = std::max<int64_t>(1, chunks * ncg * nbg);
+  const int64_t s_lo = std::max<int64_t>(1, (4 * G + per - 1) / per);
   const int64_t min_rows = std::max<int64_t>(4096, 2 * p->d);
-  const int64_t max_slices = std::max<int64_t>(1, std::min(R, rows) / min_rows);
-  return (int32_t)std::min<int64_t>(per_chunk, std::min<int64_t>(max_slices, 4096));
+  const int64_t s_max = std::min<int64_t>(std::max<int64_t>(1, std::min(R, rows) / min_rows), 4096);
+  int64_t best = std::min(s_lo, s_max);
+  double best_waste = 1e30;
+  for (int64_t sl = std::min(s_lo, s_max); sl <= std::min(4 * s_lo, s_max); ++sl) {
+    const int64_t items = per * sl;
+    const double waste = (double)((items + G - 1) / G * G) / (double)items;
+    if (waste < best_waste - 0.005) {
+      best_waste = waste;
+      best = sl;
+    }
+  }
+  return (int32_t)best;
 }
 
 // Owner-kernel configuration (atomic mode, SK_KERNEL_OWNER): blocks per item kb = 2 when two blocks
@@ -388,13 +401,11 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
   }
   L.status = p->dstatus;
   L.P = nullptr;
-  L.counters = nullptr;
   if (cfg.slices > 1) {
     int64_t chunks;
     int32_t ncg, nbg;
     tile_geometry(L, &chunks, &ncg, &nbg);
     const size_t needP = sizeof(float) * (size_t)chunks * (size_t)(p->d * n);
-    const size_t needC = sizeof(int32_t) * (size_t)(chunks * ncg * nbg);
     if (p->tileP_bytes < needP) {
       if (p->tileP) cudaFree(p->tileP);
       p->tileP = nullptr;
@@ -407,20 +418,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
       if (ez != cudaSuccess) return cuda_fail(ez, "zeroing chunk totals");
       p->tileP_bytes = needP;
     }
-    if (p->counters_bytes < needC) {
-      if (p->counters) cudaFree(p->counters);
-      p->counters = nullptr;
-      p->counters_bytes = 0;
-      if (cudaMalloc(&p->counters, needC) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(SK_ERR_OOM, "slice counters (%zu bytes)", needC);
-      }
-      cudaError_t ez = cudaMemsetAsync(p->counters, 0, needC, st);
-      if (ez != cudaSuccess) return cuda_fail(ez, "zeroing counters");
-      p->counters_bytes = needC;
-    }
     L.P = p->tileP;
-    L.counters = p->counters;
   }
   cudaError_t e = launch_tile(L, st, launches);
   if (e != cudaSuccess) return cuda_fail(e, cfg.own ? "owner kernel launch" : "tile kernel launch");
@@ -766,7 +764,6 @@ void sk_destroy(sk_plan p) {
   if (p->det_P) cudaFree(p->det_P);
   if (p->dstatus) cudaFree(p->dstatus);
   if (p->tileP) cudaFree(p->tileP);
-  if (p->counters) cudaFree(p->counters);
   if (p->solve_buf) cudaFree(p->solve_buf);
   for (int b = 0; b < 2; ++b) {
     if (p->stage[b]) cudaFree(p->stage[b]);
@@ -821,7 +818,6 @@ sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, i
   L->allow_tma = 1;
   L->status = nullptr;
   L->P = nullptr;
-  L->counters = nullptr;
   return SK_OK;
 }
 

@@ -6,6 +6,8 @@
 
 namespace sk {
 
+struct TileDesc;
+
 struct TileLaunch {
   const float* A;
   void* Y;
@@ -21,7 +23,6 @@ struct TileLaunch {
   int32_t grid;     // CTAs (0 = automatic)
   int32_t slices;   // work items per chunk (> 1: two-level combine through P)
   float* P;         // slices > 1: chunks x d x n FP32 scratch, zero on entry, zero on exit
-  int32_t* counters;  // slices > 1: chunks x nbg x ncg counters, zero on entry, zero on exit
   unsigned* status;   // sticky device status word (may be null)
   int64_t col_off;    // global column index of column 0 (keys the rounding random bits)
   int32_t allow_tma;  // stage A through TMA when its layout allows it
@@ -38,6 +39,10 @@ size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads, int32
 // the layout does not allow TMA (A not 16-byte aligned, lda % 4 != 0, too many rows).
 bool encode_a_map(void* map, const float* A, int64_t lda, int64_t n, int64_t rows, int32_t NC, int32_t RB);
 int32_t tile_slots(int32_t NC, int32_t kb);
+// Add the chunk totals of P (chunk-major, d x n FP32 each, chunks [t_first, t_first + chunks)) into
+// Y in ascending chunk order with the rule's scaling and rounding, and clear P (one launch).
+cudaError_t launch_chunk_finish(const TileDesc& D, int32_t rule, float* P, int64_t t_first, int64_t chunks,
+                                cudaStream_t st, int32_t* launches);
 // Enqueue the chunked tile kernel (atomic flush). Returns a CUDA error code.
 cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches);
 // Owner kernel (sk_own.cu): shared-memory bytes for kb blocks of B rows, threads per CTA, resident

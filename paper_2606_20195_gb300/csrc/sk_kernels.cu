@@ -18,7 +18,6 @@ namespace sk {
 template <int RULE>
 __global__ void __launch_bounds__(1024) tile_kernel(const TileGrid P, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ int last_slice;
   __shared__ int abort_flag;
   float* acc = reinterpret_cast<float*>(smem_raw);
   const int warp = threadIdx.x >> 5;
@@ -56,23 +55,9 @@ __global__ void __launch_bounds__(1024) tile_kernel(const TileGrid P, const __gr
     if (P.slices == 1) {
       tile_flush<RULE>(D, t, g, j0, kbe, acc);
     } else {
-      float* Pt = P.P + tl * dn;
-      tile_flush_partial(D, g, j0, kbe, acc, Pt);
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int32_t* cnt = P.counters + (tl * P.nbg + bg) * P.ncg + g;
-        const int prev = atomicAdd(cnt, 1);
-        last_slice = (prev == P.slices - 1);
-        if (last_slice) *cnt = 0;
-      }
-      __syncthreads();
-      if (last_slice) {
-        __threadfence();
-        tile_finish_chunk<RULE>(D, t, g, j0, kbe, Pt);
-      }
+      // slice partials into the chunk totals; chunk_finish_kernel adds them into Y after this launch
+      tile_flush_partial(D, g, j0, kbe, acc, P.P + tl * dn);
     }
-    __threadfence();
     __syncthreads();
   }
 }
@@ -158,11 +143,10 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   P.items = chunks * P.slices * P.ncg * P.nbg;
   P.acc_floats = (int32_t)tile_acc_floats((uint32_t)B, L.kb, P.D.S, L.NC);
   P.P = L.P;
-  P.counters = L.counters;
   P.status = L.status;
   P.D.col_off = L.col_off;
   P.D.tmap = nullptr;
-  if (P.slices > 1 && (!P.P || !P.counters)) return cudaErrorInvalidValue;
+  if (P.slices > 1 && !P.P) return cudaErrorInvalidValue;
   CUtensorMap tmap;
   memset(&tmap, 0, sizeof(tmap));
   const int32_t RB = 32 / (int32_t)P.D.kp;
@@ -199,6 +183,36 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   grid = std::min<int64_t>(grid, P.items);
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, L.threads, smem, st>>>(P, tmap);
+  if (launches) *launches += 1;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (P.slices > 1) return launch_chunk_finish(P.D, L.rule, P.P, P.t_first, chunks, st, launches);
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------------ chunk finish
+// One thread per output quad (row, 4 columns): the chunks of the launch in ascending order (finish_quad).
+template <int RULE>
+__global__ void __launch_bounds__(256) chunk_finish_kernel(const TileDesc D, float* P, int64_t t_first, int64_t chunks) {
+  const int64_t nq = (D.n + 3) >> 2;
+  const int64_t d = (int64_t)D.B * D.k;
+  const int64_t dn = d * D.n;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < d * nq; f += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = f / nq;
+    finish_quad<RULE>(D, (uint32_t)r, 4 * (f - r * nq), P, t_first, chunks, dn);
+  }
+}
+
+cudaError_t launch_chunk_finish(const TileDesc& D, int32_t rule, float* P, int64_t t_first, int64_t chunks,
+                                cudaStream_t st, int32_t* launches) {
+  const int64_t quads = (int64_t)D.B * D.k * ((D.n + 3) >> 2);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((quads + 255) / 256, 1 << 16));
+  switch (rule) {
+    case kRN: chunk_finish_kernel<kRN><<<grid, 256, 0, st>>>(D, P, t_first, chunks); break;
+    case kSR: chunk_finish_kernel<kSR><<<grid, 256, 0, st>>>(D, P, t_first, chunks); break;
+    case kDither: chunk_finish_kernel<kDither><<<grid, 256, 0, st>>>(D, P, t_first, chunks); break;
+    default: chunk_finish_kernel<kFP32><<<grid, 256, 0, st>>>(D, P, t_first, chunks); break;
+  }
   if (launches) *launches += 1;
   return cudaGetLastError();
 }

@@ -21,8 +21,7 @@ namespace {
 
 // 16 MiB of scratch, held by every GPU that loads this library until the process exits.
 constexpr size_t kScratchBytes = (size_t)16 << 20;
-constexpr size_t kStatusBytes = 256;            // status word, padded
-constexpr size_t kCounterBytes = (size_t)64 << 10;  // slice counters
+constexpr size_t kStatusBytes = 256;  // status word, padded
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -61,23 +60,21 @@ extern "C" SK_API sk_status sk_apply_noalloc(sk_plan p, const float* A, int64_t 
   int64_t chunks;
   int32_t ncg, nbg;
   tile_geometry(L, &chunks, &ncg, &nbg);
-  const size_t need_counters = sizeof(int32_t) * (size_t)(chunks * ncg * nbg);
   const size_t need_P = (L.slices > 1) ? sizeof(float) * (size_t)chunks * (size_t)(L.d * L.n) : 0;
-  if (need_counters > kCounterBytes || kStatusBytes + kCounterBytes + need_P > kScratchBytes)
+  if (kStatusBytes + need_P > kScratchBytes)
     return set_error(SK_ERR_UNSUPPORTED,
                      "sk_apply_noalloc: this size needs %zu bytes of scratch, above the %zu-byte static array; "
                      "use sk_apply",
-                     kStatusBytes + kCounterBytes + need_P, kScratchBytes);
+                     kStatusBytes + need_P, kScratchBytes);
   unsigned char* b = static_cast<unsigned char*>(base);
   cudaStream_t st = (cudaStream_t)stream;
   // The array keeps the previous call's contents: clear what this call needs at zero.
   cudaError_t e = cudaMemsetAsync(Y, 0, noalloc_elem_size(p) * (size_t)(L.d * L.n), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, kStatusBytes + need_counters, st);
-  if (e == cudaSuccess && need_P) e = cudaMemsetAsync(b + kStatusBytes + kCounterBytes, 0, need_P, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, kStatusBytes, st);
+  if (e == cudaSuccess && need_P) e = cudaMemsetAsync(b + kStatusBytes, 0, need_P, st);
   if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "zeroing: %s", cudaGetErrorString(e));
   L.status = reinterpret_cast<unsigned*>(b);
-  L.counters = reinterpret_cast<int32_t*>(b + kStatusBytes);
-  L.P = need_P ? reinterpret_cast<float*>(b + kStatusBytes + kCounterBytes) : nullptr;
+  L.P = need_P ? reinterpret_cast<float*>(b + kStatusBytes) : nullptr;
   int32_t launches = 0;
   e = launch_tile(L, st, &launches);
   if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "tile kernel launch: %s", cudaGetErrorString(e));

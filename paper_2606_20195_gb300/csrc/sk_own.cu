@@ -57,7 +57,6 @@ __host__ __device__ inline OwnSmem own_smem(int64_t acc_floats) {
 template <int RULE>
 __global__ void __launch_bounds__(kOwnThreads, 1) own_kernel(const TileGrid P, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ int last_slice;
   __shared__ int abort_flag;
   const OwnSmem SL = own_smem(P.acc_floats);
   float* acc = reinterpret_cast<float*>(smem_raw + SL.acc_off);
@@ -196,23 +195,9 @@ __global__ void __launch_bounds__(kOwnThreads, 1) own_kernel(const TileGrid P, c
     if (P.slices == 1) {
       tile_flush<RULE>(D, t, g, j0, kbe, acc);
     } else {
-      float* Pt = P.P + tl * dn;
-      tile_flush_partial(D, g, j0, kbe, acc, Pt);
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int32_t* cnt = P.counters + (tl * P.nbg + bg) * P.ncg + g;
-        const int prev = atomicAdd(cnt, 1);
-        last_slice = (prev == P.slices - 1);
-        if (last_slice) *cnt = 0;
-      }
-      __syncthreads();
-      if (last_slice) {
-        __threadfence();
-        tile_finish_chunk<RULE>(D, t, g, j0, kbe, Pt);
-      }
+      // slice partials into the chunk totals; the chunk-finish kernel adds them into Y afterwards
+      tile_flush_partial(D, g, j0, kbe, acc, P.P + tl * dn);
     }
-    __threadfence();
     __syncthreads();
   }
 }
@@ -281,10 +266,9 @@ cudaError_t launch_own(const TileLaunch& L, cudaStream_t st, int32_t* launches) 
   P.items = chunks * P.slices * P.ncg * P.nbg;
   P.acc_floats = (int32_t)((int64_t)L.kb * B * 32);
   P.P = L.P;
-  P.counters = L.counters;
   P.status = L.status;
   P.depth = kOwnDepth;
-  if (P.slices > 1 && (!P.P || !P.counters)) return cudaErrorInvalidValue;
+  if (P.slices > 1 && !P.P) return cudaErrorInvalidValue;
   CUtensorMap tmap;
   memset(&tmap, 0, sizeof(tmap));
   if (!encode_a_map(&tmap, L.A, L.lda, L.n, L.row_end - L.row_begin, 32, kOwnStageRows)) return cudaErrorInvalidValue;
@@ -308,7 +292,10 @@ cudaError_t launch_own(const TileLaunch& L, cudaStream_t st, int32_t* launches) 
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, kOwnThreads, smem, st>>>(P, tmap);
   if (launches) *launches += 1;
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (P.slices > 1) return launch_chunk_finish(P.D, L.rule, P.P, P.t_first, chunks, st, launches);
+  return cudaSuccess;
 }
 
 }  // namespace sk

@@ -56,7 +56,6 @@ struct TileGrid {
   int32_t ncg, nbg, slices;
   int32_t acc_floats;          // floats of the accumulator (multiple of 4)
   float* P;                    // slices > 1: per-chunk FP32 totals, chunk-major, d x n each (zero)
-  int32_t* counters;           // slices > 1: finished slices per (chunk, bg, g) (zero)
   unsigned* status;            // sticky status word (kStatus*), may be null
   int32_t use_tma;             // 1: A arrives through the tensor map
   int32_t depth;               // TMA ring slots per warp
@@ -561,26 +560,17 @@ __device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int6
   return tile_scatter_t<0>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
 }
 
-// Scale, quantize and add four consecutive columns of output row r (chunk t) into Y: one Philox
-// call gives the four uniforms, FP32 adds use one 16-byte vector reduction, FP16 adds two packed
-// half2 atomics (paper Listing 2).
+// Scale and (FP16 rules) quantize four consecutive columns of output row r (chunk t): x = fl32(scale
+// * v) for FP32, else the binary16 values of the rule with one Philox call giving the four uniforms
+// (paper Sec. 4.2).
 template <int RULE>
-__device__ __forceinline__ void emit_quad(const TileDesc& D, uint32_t r, int64_t col0, float4 v, int64_t t) {
-  const int64_t n = D.n;
-  const float x0 = __fmul_rn(D.scale, v.x), x1 = __fmul_rn(D.scale, v.y);
-  const float x2 = __fmul_rn(D.scale, v.z), x3 = __fmul_rn(D.scale, v.w);
-  if (RULE == kFP32) {
-    float* y = reinterpret_cast<float*>(D.Y) + (int64_t)r * n + col0;
-    if ((n & 3) == 0 && col0 + 3 < n) {
-      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(y), "f"(x0), "f"(x1), "f"(x2), "f"(x3)
-                   : "memory");
-    } else {
-      atomicAdd(y, x0);
-      if (col0 + 1 < n) atomicAdd(y + 1, x1);
-      if (col0 + 2 < n) atomicAdd(y + 2, x2);
-      if (col0 + 3 < n) atomicAdd(y + 3, x3);
-    }
-  } else {
+__device__ __forceinline__ void scale_quad(const TileDesc& D, uint32_t r, int64_t col0, float4 v, int64_t t, float x[4],
+                                           __half q[4]) {
+  x[0] = __fmul_rn(D.scale, v.x);
+  x[1] = __fmul_rn(D.scale, v.y);
+  x[2] = __fmul_rn(D.scale, v.z);
+  x[3] = __fmul_rn(D.scale, v.w);
+  if (RULE != kFP32) {
     float u[4] = {0.f, 0.f, 0.f, 0.f};
     if (RULE != kRN) {
       // Columns col_off + col0 .. +3 of the global column space; their uniforms come from at most
@@ -597,20 +587,105 @@ __device__ __forceinline__ void emit_quad(const TileDesc& D, uint32_t r, int64_t
         for (int e = 0; e < 4; ++e) u[e] = (o + e < 4) ? ua[o + e] : ub[o + e - 4];
       }
     }
-    const __half q0 = quantize<RULE>(x0, u[0]);
-    const __half q1 = quantize<RULE>(x1, u[1]);
-    const __half q2 = quantize<RULE>(x2, u[2]);
-    const __half q3 = quantize<RULE>(x3, u[3]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) q[e] = quantize<RULE>(x[e], u[e]);
+  }
+}
+
+// Scale, quantize and add four consecutive columns of output row r (chunk t) into Y: FP32 adds use
+// one 16-byte vector reduction, FP16 adds two packed half2 atomics (paper Listing 2).
+template <int RULE>
+__device__ __forceinline__ void emit_quad(const TileDesc& D, uint32_t r, int64_t col0, float4 v, int64_t t) {
+  const int64_t n = D.n;
+  float x[4];
+  __half q[4];
+  scale_quad<RULE>(D, r, col0, v, t, x, q);
+  if (RULE == kFP32) {
+    float* y = reinterpret_cast<float*>(D.Y) + (int64_t)r * n + col0;
+    if ((n & 3) == 0 && col0 + 3 < n) {
+      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(y), "f"(x[0]), "f"(x[1]), "f"(x[2]),
+                   "f"(x[3])
+                   : "memory");
+    } else {
+      atomicAdd(y, x[0]);
+      if (col0 + 1 < n) atomicAdd(y + 1, x[1]);
+      if (col0 + 2 < n) atomicAdd(y + 2, x[2]);
+      if (col0 + 3 < n) atomicAdd(y + 3, x[3]);
+    }
+  } else {
     __half* y = reinterpret_cast<__half*>(D.Y) + (int64_t)r * n + col0;
     if ((n & 1) == 0) {
-      atomicAdd(reinterpret_cast<__half2*>(y), __halves2half2(q0, q1));  // col0 + 1 < n since n even
-      if (col0 + 3 < n) atomicAdd(reinterpret_cast<__half2*>(y + 2), __halves2half2(q2, q3));
+      atomicAdd(reinterpret_cast<__half2*>(y), __halves2half2(q[0], q[1]));  // col0 + 1 < n since n even
+      if (col0 + 3 < n) atomicAdd(reinterpret_cast<__half2*>(y + 2), __halves2half2(q[2], q[3]));
     } else {
-      atomicAdd(y, q0);
-      if (col0 + 1 < n) atomicAdd(y + 1, q1);
-      if (col0 + 2 < n) atomicAdd(y + 2, q2);
-      if (col0 + 3 < n) atomicAdd(y + 3, q3);
+      atomicAdd(y, q[0]);
+      if (col0 + 1 < n) atomicAdd(y + 1, q[1]);
+      if (col0 + 2 < n) atomicAdd(y + 2, q[2]);
+      if (col0 + 3 < n) atomicAdd(y + 3, q[3]);
     }
+  }
+}
+
+// Finish the chunks [t_first, t_first + chunks) of one output quad (row r, columns col0 .. col0+3):
+// in ascending chunk order, read the chunk total from P (chunk-major, d x n each), clear it, scale,
+// quantize and add it into Y with the rule's arithmetic (binary32 add or binary16 add, round to
+// nearest), then write Y back once. Chunk totals that are zero in all four columns add nothing.
+template <int RULE>
+__device__ __forceinline__ void finish_quad(const TileDesc& D, uint32_t r, int64_t col0, float* P, int64_t t_first,
+                                            int64_t chunks, int64_t dn) {
+  const int64_t n = D.n;
+  const int ne = (int)min((int64_t)4, n - col0);
+  const bool vec = (n & 3) == 0;
+  const int64_t off = (int64_t)r * n + col0;
+  float yf[4] = {0.f, 0.f, 0.f, 0.f};
+  __half yh[4];
+  bool loaded = false, touched = false;
+  for (int64_t tl = 0; tl < chunks; ++tl) {
+    float* p = P + tl * dn + off;
+    float4 v;
+    if (vec) {
+      v = __ldcg(reinterpret_cast<const float4*>(p));
+    } else {
+      v.x = __ldcg(p);
+      v.y = ne > 1 ? __ldcg(p + 1) : 0.f;
+      v.z = ne > 2 ? __ldcg(p + 2) : 0.f;
+      v.w = ne > 3 ? __ldcg(p + 3) : 0.f;
+    }
+    if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+    if (vec) {
+      __stcg(reinterpret_cast<float4*>(p), make_float4(0.f, 0.f, 0.f, 0.f));
+    } else {
+      for (int e = 0; e < ne; ++e) __stcg(p + e, 0.f);
+    }
+    if (!loaded) {
+      loaded = true;
+      if (RULE == kFP32) {
+        const float* y = reinterpret_cast<const float*>(D.Y) + off;
+        for (int e = 0; e < ne; ++e) yf[e] = y[e];
+      } else {
+        const __half* y = reinterpret_cast<const __half*>(D.Y) + off;
+        for (int e = 0; e < ne; ++e) yh[e] = y[e];
+      }
+    }
+    float x[4];
+    __half q[4];
+    scale_quad<RULE>(D, r, col0, v, t_first + tl, x, q);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (e < ne) {
+        if (RULE == kFP32) yf[e] = __fadd_rn(yf[e], x[e]);
+        else yh[e] = __hadd(yh[e], q[e]);
+      }
+    }
+    touched = true;
+  }
+  if (!touched) return;
+  if (RULE == kFP32) {
+    float* y = reinterpret_cast<float*>(D.Y) + off;
+    for (int e = 0; e < ne; ++e) y[e] = yf[e];
+  } else {
+    __half* y = reinterpret_cast<__half*>(D.Y) + off;
+    for (int e = 0; e < ne; ++e) y[e] = yh[e];
   }
 }
 
@@ -705,36 +780,6 @@ __device__ __forceinline__ void tile_flush_partial(const TileDesc& D, int32_t g,
       if (col0 + 2 < n) atomicAdd(y + 2, v.z);
       if (col0 + 3 < n) atomicAdd(y + 3, v.w);
     }
-  }
-}
-
-// Last slice of a chunk done: read the chunk totals of this (column group, block group) region of
-// P, quantize and add them into Y, and restore P to zero for the next use.
-template <int RULE>
-__device__ __forceinline__ void tile_finish_chunk(const TileDesc& D, int64_t t, int32_t g, int32_t j0, int32_t kbe,
-                                                  float* P) {
-  const int NC = 1 << D.log2NC;
-  const int nq = NC >> 2;
-  const int64_t n = D.n;
-  const int64_t total = (int64_t)kbe * D.B * nq;
-  for (int64_t f = threadIdx.x; f < total; f += blockDim.x) {
-    const int c4 = (int)(f % nq);
-    const int64_t rr = f / nq;
-    const uint32_t r = (uint32_t)j0 * D.B + (uint32_t)rr;
-    const int64_t col0 = (int64_t)g * NC + 4 * c4;
-    if (col0 >= n) continue;
-    float* y = P + (int64_t)r * n + col0;
-    float4 v;
-    v.x = __ldcg(y);
-    v.y = (col0 + 1 < n) ? __ldcg(y + 1) : 0.f;
-    v.z = (col0 + 2 < n) ? __ldcg(y + 2) : 0.f;
-    v.w = (col0 + 3 < n) ? __ldcg(y + 3) : 0.f;
-    if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
-    y[0] = 0.f;
-    if (col0 + 1 < n) y[1] = 0.f;
-    if (col0 + 2 < n) y[2] = 0.f;
-    if (col0 + 3 < n) y[3] = 0.f;
-    emit_quad<RULE>(D, r, col0, v, t);
   }
 }
 
