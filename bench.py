@@ -372,7 +372,8 @@ def main() -> int:
     launches_per_step = plan.get(sk.SK_PARAM_LAST_LAUNCHES)
     R_used = plan.get(sk.SK_PARAM_LAST_CHUNK_ROWS)
     kernel_name = {sk.SK_KERNEL_TILE: "tile_kernel", sk.SK_KERNEL_OWNER: "own_kernel",
-                   sk.SK_KERNEL_LITERAL: "literal_kernel"}.get(plan.get(sk.SK_PARAM_LAST_KERNEL), "det_kernel")
+                   sk.SK_KERNEL_LITERAL: "literal_kernel", sk.SK_KERNEL_GLOBAL: "global_kernel"}.get(
+                       plan.get(sk.SK_PARAM_LAST_KERNEL), "det_kernel")
     t = torch.tensor([total_ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -78,7 +78,10 @@ typedef enum {
    * accumulator row has one owning warp: no atomics; needs n >= 32, A 16-byte aligned with lda a
    * multiple of 4, and B*128 bytes of shared memory per block; SK_ERR_UNSUPPORTED otherwise).
    * Inside a work item the owner kernel adds rows in ascending order, so a chunk processed as one
-   * work item has exactly the canonical FP32 chunk total. AUTO takes the tile kernel. */
+   * work item has exactly the canonical FP32 chunk total. SK_KERNEL_GLOBAL (chunk totals
+   * accumulated in device memory with FP32 reductions, one warp per row; any block height). AUTO
+   * takes the tile kernel, or the global kernel when a block of S is too tall for the tile
+   * kernel's shared-memory accumulator. */
   SK_PARAM_KERNEL = 4,
   /* Columns per work item of the tile kernel (4, 8, 16 or 32; 0 = automatic). */
   SK_PARAM_TILE_COLS = 5,
@@ -92,12 +95,13 @@ typedef enum {
    * bounded wait gave up, the results of that call are invalid). Reading it synchronizes the device. */
   SK_PARAM_DEVICE_STATUS = 9,
   /* Read-only: the kernel the last sketch ran: SK_KERNEL_TILE (1), SK_KERNEL_LITERAL (2),
-   * SK_KERNEL_OWNER (3), or 4 for the deterministic-mode kernel; 0 before the first sketch. */
+   * SK_KERNEL_OWNER (3), SK_KERNEL_GLOBAL (4), or 5 for the deterministic-mode kernel; 0 before the
+   * first sketch. */
   SK_PARAM_LAST_KERNEL = 10
 } sk_param;
 
 enum { SK_MODE_ATOMIC = 0, SK_MODE_DETERMINISTIC = 1, SK_MODE_SERIAL_TILE = 2 };
-enum { SK_KERNEL_AUTO = 0, SK_KERNEL_TILE = 1, SK_KERNEL_LITERAL = 2, SK_KERNEL_OWNER = 3 };
+enum { SK_KERNEL_AUTO = 0, SK_KERNEL_TILE = 1, SK_KERNEL_LITERAL = 2, SK_KERNEL_OWNER = 3, SK_KERNEL_GLOBAL = 4 };
 
 typedef struct sk_plan_s* sk_plan;
 

@@ -49,7 +49,7 @@ struct sk_plan_s {
   int32_t tile_cols = 0;
   int32_t threads = 0;
   int64_t last_launches = 0, last_R = 0;
-  int32_t last_kernel = 0;  // kernel of the last sketch: 1 tile, 2 literal, 3 owner, 4 deterministic
+  int32_t last_kernel = 0;  // kernel of the last sketch: 1 tile, 2 literal, 3 owner, 4 global, 5 deterministic
   // device scratch
   float* det_P = nullptr;
   size_t det_P_bytes = 0;
@@ -102,6 +102,7 @@ struct TileCfg {
   bool lr = false;
   bool own = false;
   bool vec = false;
+  bool glob = false;
 };
 
 // Default chunk length: at most 8 chunks per matrix (each output then receives at most 8 rounded
@@ -174,8 +175,24 @@ bool choose_own(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, 
   return true;
 }
 
+// Global-accumulator configuration: chunk totals in device memory (any block height).
+void choose_global(const sk_plan_s* p, TileCfg* cfg) {
+  *cfg = TileCfg();
+  cfg->NC = 4;
+  cfg->kb = p->k;
+  cfg->threads = 256;
+  cfg->R = p->R > 0 ? p->R : default_chunk_rows(p->m);
+  cfg->slices = 1;
+  cfg->glob = true;
+}
+
 sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, TileCfg* cfg,
                       bool tma_ok = false) {
+  if (p->kernel == SK_KERNEL_GLOBAL) {
+    if (p->mode != SK_MODE_ATOMIC) return set_error(SK_ERR_UNSUPPORTED, "the global kernel runs in atomic mode only");
+    choose_global(p, cfg);
+    return SK_OK;
+  }
   if (choose_own(p, n, rows, di, tma_ok, cfg)) return SK_OK;
   if (p->kernel == SK_KERNEL_OWNER)
     return set_error(SK_ERR_UNSUPPORTED,
@@ -244,10 +261,16 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
       }
     }
   }
-  if (NC == 0 || kb == 0)
+  if (NC == 0 || kb == 0) {
+    // A block too tall for the on-chip accumulator: chunk totals in device memory instead.
+    if (!serial && p->kernel == SK_KERNEL_AUTO) {
+      choose_global(p, cfg);
+      return SK_OK;
+    }
     return set_error(SK_ERR_UNSUPPORTED,
                      "tile kernel: a block of %lld rows does not fit in shared memory with the requested width",
                      (long long)p->B);
+  }
   // One block group (outside serial mode): every work item takes the lane-row path, with several
   // hash rounds per TMA box (boxes of up to 1 KiB).
   const bool lr = !serial && kb == p->k;
@@ -337,7 +360,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
     L.col_off = col_off;
     cudaError_t e = launch_det(L, st, launches);
     if (e != cudaSuccess) return cuda_fail(e, "deterministic kernel launch");
-    p->last_kernel = 4;
+    p->last_kernel = 5;
     if (R_used) *R_used = R;
     return SK_OK;
   }
@@ -389,6 +412,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
   L.lr = cfg.lr ? 1 : 0;
   L.own = cfg.own ? 1 : 0;
   L.vec = cfg.vec ? 1 : 0;
+  L.glob = cfg.glob ? 1 : 0;
   L.col_off = col_off;
   L.allow_tma = cfg.vec ? 0 : 1;
   if (!p->dstatus) {
@@ -401,7 +425,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
   }
   L.status = p->dstatus;
   L.P = nullptr;
-  if (cfg.slices > 1) {
+  if (cfg.slices > 1 || cfg.glob) {
     int64_t chunks;
     int32_t ncg, nbg;
     tile_geometry(L, &chunks, &ncg, &nbg);
@@ -421,8 +445,8 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
     L.P = p->tileP;
   }
   cudaError_t e = launch_tile(L, st, launches);
-  if (e != cudaSuccess) return cuda_fail(e, cfg.own ? "owner kernel launch" : "tile kernel launch");
-  p->last_kernel = cfg.own ? SK_KERNEL_OWNER : SK_KERNEL_TILE;
+  if (e != cudaSuccess) return cuda_fail(e, cfg.glob ? "global kernel launch" : cfg.own ? "owner kernel launch" : "tile kernel launch");
+  p->last_kernel = cfg.glob ? SK_KERNEL_GLOBAL : cfg.own ? SK_KERNEL_OWNER : SK_KERNEL_TILE;
   if (R_used) *R_used = cfg.R;
   return SK_OK;
 }
@@ -475,7 +499,7 @@ sk_status sk_plan_set(sk_plan p, int32_t key, int64_t v) {
       p->row_offset = v;
       return SK_OK;
     case SK_PARAM_KERNEL:
-      if (v < SK_KERNEL_AUTO || v > SK_KERNEL_OWNER) return set_error(SK_ERR_INVALID_ARG, "unknown kernel %lld", (long long)v);
+      if (v < SK_KERNEL_AUTO || v > SK_KERNEL_GLOBAL) return set_error(SK_ERR_INVALID_ARG, "unknown kernel %lld", (long long)v);
       p->kernel = (int32_t)v;
       return SK_OK;
     case SK_PARAM_TILE_COLS:
@@ -814,6 +838,7 @@ sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, i
   L->lr = cfg.lr ? 1 : 0;
   L->own = cfg.own ? 1 : 0;
   L->vec = cfg.vec ? 1 : 0;
+  L->glob = cfg.glob ? 1 : 0;
   L->col_off = 0;
   L->allow_tma = 1;
   L->status = nullptr;
@@ -823,10 +848,10 @@ sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, i
 
 size_t noalloc_elem_size(const sk_plan_s* p) { return elem_size(p->rule); }
 
-void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R, bool own) {
+void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R, int32_t kernel) {
   p->last_launches = launches;
   p->last_R = R;
-  p->last_kernel = own ? SK_KERNEL_OWNER : SK_KERNEL_TILE;
+  p->last_kernel = kernel;
 }
 
 }  // namespace sk

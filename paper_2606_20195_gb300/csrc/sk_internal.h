@@ -31,6 +31,7 @@ struct TileLaunch {
   int32_t lr = 0;     // 1: lane-row scatter (one block group; used only when A is staged through TMA)
   int32_t own = 0;    // 1: owner kernel (NC = 32, kb = 1 or 2 blocks per item, A through TMA)
   int32_t vec = 0;    // 1: n = 1 vector path of the tile kernel (NC = 4, no TMA)
+  int32_t glob = 0;   // 1: global-accumulator kernel (chunk totals in P, any d); needs P
 };
 
 // Shared-memory bytes the tile kernel needs for (B, kb, NC, threads, k, ring depth, rounds per box).

@@ -116,7 +116,109 @@ void tile_geometry(const TileLaunch& L, int64_t* chunks, int32_t* ncg, int32_t* 
   *nbg = (L.k + L.kb - 1) / L.kb;
 }
 
+// ------------------------------------------------------------------ global-accumulator kernel
+// For blocks too tall for an on-chip accumulator (B x 4 columns of FP32 beyond shared memory): one warp
+// per input row (grid-stride over the rows). Lane j < k evaluates block j's word of the row (stream
+// output i*kp + j/2 + 1), the lanes then take the row's 4-column quads in turns and add each signed
+// quad into the chunk total P[t - t_first][target][...] with one red.global.add.v4.f32 (scalar FP32
+// reductions for a ragged last quad or n % 4 != 0). Contributions reach each chunk total in any order
+// (atomic mode); chunk_finish_kernel then adds the totals into Y in chunk order.
+__global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P, int64_t row_end, int64_t R,
+                                                     int64_t t_first) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n = D.n;
+  const int64_t nq = (n + 3) >> 2;
+  const int k = (int)D.k;
+  const int64_t dn = (int64_t)D.B * D.k * n;
+  const bool vec = (n & 3) == 0 && (D.lda & 3) == 0 && (reinterpret_cast<uintptr_t>(D.A) & 15u) == 0;
+  for (int64_t i = D.row_base + wg; i < row_end; i += nw) {
+    float* Pt = P + (i / R - t_first) * dn;
+    const float* arow = D.A + (i - D.row_base) * D.lda;
+    for (int jb = 0; jb < k; jb += 32) {
+      // this lane's block jb + lane: target row (with the block offset) and sign bit
+      uint32_t tw = 0;
+      const int jl = jb + lane;
+      if (jl < k) {
+        const uint32_t w = block_word(row_pair_bits(D.seed, (uint64_t)i, D.kp, (uint32_t)jl >> 1), (uint32_t)jl);
+        tw = ((uint32_t)jl * D.B + word_to_slot(w, D.B)) | (w << 31);
+      }
+      const int kk = min(32, k - jb);
+      for (int64_t q0 = 0; q0 < nq; q0 += 32) {
+        const int64_t q = q0 + lane;
+        const bool active = q < nq;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int64_t col0 = 4 * q;
+        if (active) {
+          if (vec) {
+            a = __ldg(reinterpret_cast<const float4*>(arow + col0));
+          } else {
+            a.x = __ldg(arow + col0);
+            if (col0 + 1 < n) a.y = __ldg(arow + col0 + 1);
+            if (col0 + 2 < n) a.z = __ldg(arow + col0 + 2);
+            if (col0 + 3 < n) a.w = __ldg(arow + col0 + 3);
+          }
+        }
+        for (int jj = 0; jj < kk; ++jj) {
+          const uint32_t t = __shfl_sync(0xffffffffu, tw, jj);
+          if (!active) continue;
+          const uint32_t sg = t & 0x80000000u;
+          float* p = Pt + (int64_t)(t & 0x7FFFFFFFu) * n + col0;
+          const float x = __uint_as_float(__float_as_uint(a.x) ^ sg), y = __uint_as_float(__float_as_uint(a.y) ^ sg);
+          const float z = __uint_as_float(__float_as_uint(a.z) ^ sg), w4 = __uint_as_float(__float_as_uint(a.w) ^ sg);
+          if ((n & 3) == 0) {
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w4)
+                         : "memory");
+          } else {
+            atomicAdd(p, x);
+            if (col0 + 1 < n) atomicAdd(p + 1, y);
+            if (col0 + 2 < n) atomicAdd(p + 2, z);
+            if (col0 + 3 < n) atomicAdd(p + 3, w4);
+          }
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_global(const TileLaunch& L, cudaStream_t st, int32_t* launches) {
+  if (!L.P) return cudaErrorInvalidValue;
+  TileDesc D;
+  memset(&D, 0, sizeof(D));
+  const int64_t B = L.d / L.k;
+  D.A = L.A;
+  D.Y = L.Y;
+  D.lda = L.lda;
+  D.n = L.n;
+  D.row_base = L.row_begin;
+  D.seed = L.seed;
+  D.scale = L.scale;
+  D.B = (uint32_t)B;
+  D.k = (uint32_t)L.k;
+  D.kp = (uint32_t)((L.k + 1) / 2);
+  D.log2NC = 2;
+  D.S = 1;
+  D.kb = L.k;
+  D.col_off = L.col_off;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t rows = L.row_end - L.row_begin;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, (int64_t)sms * 8));
+  const int64_t t_first = L.row_begin / L.R;
+  global_kernel<<<(unsigned)grid, 256, 0, st>>>(D, L.P, L.row_end, L.R, t_first);
+  if (launches) *launches += 1;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t chunks = (L.row_end - 1) / L.R - t_first + 1;
+  return launch_chunk_finish(D, L.rule, L.P, t_first, chunks, st, launches);
+}
+
 cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches) {
+  if (L.glob) return launch_global(L, st, launches);
   if (L.own) return launch_own(L, st, launches);
   TileGrid P;
   const int64_t B = L.d / L.k;

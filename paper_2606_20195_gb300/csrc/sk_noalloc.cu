@@ -12,7 +12,7 @@
 namespace sk {
 sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, int64_t n, void* Y, TileLaunch* L);
 size_t noalloc_elem_size(const sk_plan_s* p);
-void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R, bool own);
+void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R, int32_t kernel);
 }  // namespace sk
 
 using namespace sk;
@@ -60,7 +60,7 @@ extern "C" SK_API sk_status sk_apply_noalloc(sk_plan p, const float* A, int64_t 
   int64_t chunks;
   int32_t ncg, nbg;
   tile_geometry(L, &chunks, &ncg, &nbg);
-  const size_t need_P = (L.slices > 1) ? sizeof(float) * (size_t)chunks * (size_t)(L.d * L.n) : 0;
+  const size_t need_P = (L.slices > 1 || L.glob) ? sizeof(float) * (size_t)chunks * (size_t)(L.d * L.n) : 0;
   if (kStatusBytes + need_P > kScratchBytes)
     return set_error(SK_ERR_UNSUPPORTED,
                      "sk_apply_noalloc: this size needs %zu bytes of scratch, above the %zu-byte static array; "
@@ -77,7 +77,7 @@ extern "C" SK_API sk_status sk_apply_noalloc(sk_plan p, const float* A, int64_t 
   L.P = need_P ? reinterpret_cast<float*>(b + kStatusBytes) : nullptr;
   int32_t launches = 0;
   e = launch_tile(L, st, &launches);
-  if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "tile kernel launch: %s", cudaGetErrorString(e));
-  noalloc_record(p, launches, L.R, L.own != 0);
+  if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "sketch kernel launch: %s", cudaGetErrorString(e));
+  noalloc_record(p, launches, L.R, L.glob ? SK_KERNEL_GLOBAL : L.own ? SK_KERNEL_OWNER : SK_KERNEL_TILE);
   return SK_OK;
 }

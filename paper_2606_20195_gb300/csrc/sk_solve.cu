@@ -10,7 +10,7 @@
 // publishes that row before the barrier; after the last step every owner writes its final rows of R
 // and CTA 0 finishes with the back substitution R x = (Q^T Sb)[:n].
 //
-// Every grid barrier spins with an iteration limit: on expiry the kernel sets kStatusTimeout in
+// Every grid barrier waits at most about two seconds: on expiry the kernel sets kStatusTimeout in
 // the status word and all CTAs leave at the next check, so a stalled launch cannot hang the GPU.
 #include <cuda_fp16.h>
 
@@ -23,16 +23,26 @@ namespace sk {
 
 namespace {
 
-constexpr long long kSpinLimit = 1ll << 26;  // iterations of short sleeps (a few seconds)
+// Columns of W = [SA | Sb] the kernel handles (n + 1 <= kQRMaxCols).
+constexpr int kQRMaxCols = 520;
+
+// A grid barrier gives up after about two seconds of waiting (in SM clock cycles at ~2 GHz).
+constexpr long long kBarrierCycles = 4000000000ll;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 
 // Grid barrier for a co-resident (cooperative) grid. bar[0]: arrivals, bar[1]: generation.
-// Returns false if this CTA, or any CTA before it, gave up waiting.
+// Waiters poll the generation with acquire loads (short sleeps only after the first few hundred
+// polls). Returns false if this CTA, or any CTA before it, gave up waiting.
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g0 = *gen;
+    const unsigned g0 = ld_acquire_u32(bar + 1);
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u);
     if (arrived == nblocks - 1) {
@@ -40,15 +50,18 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) 
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
-      long long spins = 0;
-      while (*gen == g0) {
-        if (++spins > kSpinLimit) {
-          atomicOr(status, kStatusTimeout);
-          break;
+      const long long t0 = clock64();
+      unsigned polls = 0;
+      while (ld_acquire_u32(bar + 1) == g0) {
+        if ((++polls & 255u) == 0) {
+          if (clock64() - t0 > kBarrierCycles) {
+            atomicOr(status, kStatusTimeout);
+            break;
+          }
+          // Another CTA already gave up: stop waiting.
+          if (*(volatile unsigned*)status & kStatusTimeout) break;
         }
-        // Another CTA already gave up: stop waiting.
-        if ((spins & 1023) == 0 && (*(volatile unsigned*)status & kStatusTimeout)) break;
-        __nanosleep(20);
+        if (polls > 512) __nanosleep(32);
       }
     }
     __threadfence();
@@ -95,6 +108,7 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
   extern __shared__ __align__(16) double Wl[];  // rpc x (n+1), row-major
   __shared__ double red[32];
   __shared__ double sc[4];
+  __shared__ double wsm[kQRMaxCols];  // w_c = v^T W[:, c] of the current column step
   const SolveLaunch& L = a.L;
   const int64_t n = L.n, d = L.d, ldw = n + 1;
   const int b = blockIdx.x;
@@ -147,16 +161,18 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
     }
     __syncthreads();
     const double alpha = sc[0], vj = sc[1], tau = sc[2];
-    // W[r][c] -= tau v_r w_c with w_c = v^T W[:, c] = x^T W[:, c] - alpha W[j][c].
+    // W[r][c] -= tau v_r w_c with w_c = v^T W[:, c] = x^T W[:, c] - alpha W[j][c] (staged once per CTA).
     if (tau != 0.0) {
+      for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x)
+        wsm[c] = __ldcg(&a.wv[j * ldw + c]) - alpha * __ldcg(&L.R[j * ldw + c]);
+      __syncthreads();
       const int64_t ncols = n - j;  // columns j+1 .. n
       for (int64_t e = threadIdx.x; e < nown * ncols; e += blockDim.x) {
         const int64_t rl = e / ncols, c = j + 1 + (e - rl * ncols);
         const int64_t r = row0 + rl;
         if (r < j) continue;
-        const double wc = __ldcg(&a.wv[j * ldw + c]) - alpha * __ldcg(&L.R[j * ldw + c]);
         const double vr = (r == j) ? vj : Wl[rl * ldw + j];
-        Wl[rl * ldw + c] -= tau * vr * wc;
+        Wl[rl * ldw + c] -= tau * vr * wsm[c];
       }
     }
     __syncthreads();
@@ -211,8 +227,8 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
 }  // namespace
 
 int32_t solve_ctas(int64_t d, int64_t n, int32_t sms, size_t smem_optin) {
-  if (n < 1 || d < n) return 0;
-  const size_t budget = smem_optin > 4096 ? smem_optin - 4096 : 0;
+  if (n < 1 || d < n || n + 1 > kQRMaxCols) return 0;
+  const size_t budget = smem_optin > 10240 ? smem_optin - 10240 : 0;  // static shared memory and margin
   int64_t ncta = std::min<int64_t>(sms, std::max<int64_t>(1, (d + 7) / 8));
   for (; ncta <= sms; ++ncta) {
     const int64_t rpc = (d + ncta - 1) / ncta;
