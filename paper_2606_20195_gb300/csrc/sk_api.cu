@@ -271,6 +271,13 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
                      "tile kernel: a block of %lld rows does not fit in shared memory with the requested width",
                      (long long)p->B);
   }
+  // Where the tile kernel would need several block groups (the target-word scatter, 5-7x slower
+  // than the global kernel at n = 1024 and d >= 16384), or only 4-column items for a wide matrix
+  // (each row's hash evaluated n/4 times), AUTO takes the global-accumulator kernel.
+  if (!serial && p->kernel == SK_KERNEL_AUTO && p->tile_cols == 0 && (kb < p->k || (NC <= 4 && n >= 256))) {
+    choose_global(p, cfg);
+    return SK_OK;
+  }
   // One block group (outside serial mode): every work item takes the lane-row path, with several
   // hash rounds per TMA box (boxes of up to 1 KiB).
   const bool lr = !serial && kb == p->k;
