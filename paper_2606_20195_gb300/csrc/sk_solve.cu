@@ -6,12 +6,13 @@
 // are split across the CTAs (one per SM at most); each CTA keeps its rows of W in shared memory
 // for the whole factorization. Column step j needs one grid-wide reduction: the partial sums of
 // x^T x and x^T W[:, c] (x = column j below the diagonal) give both the reflector and v^T W[:, c],
-// accumulated with FP64 atomics into per-step buffers, followed by one grid barrier. The owner of row j
+// accumulated with FP64 atomics into per-step buffers, followed by one grid synchronization. The owner of row j
 // publishes that row before the barrier; after the last step every owner writes its final rows of R
 // and CTA 0 finishes with the back substitution R x = (Q^T Sb)[:n].
 //
-// Every grid barrier waits at most about two seconds: on expiry the kernel sets kStatusTimeout in
-// the status word and all CTAs leave at the next check, so a stalled launch cannot hang the GPU.
+// Every grid synchronization waits at most about two seconds: on expiry the kernel sets
+// kStatusTimeout in the status word and all CTAs leave at the next check, so a stalled launch cannot
+// hang the GPU.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -35,36 +36,29 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// Grid barrier for a co-resident (cooperative) grid. bar[0]: arrivals, bar[1]: generation.
-// Waiters poll the generation with acquire loads (short sleeps only after the first few hundred
-// polls). Returns false if this CTA, or any CTA before it, gave up waiting.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) {
+// Grid synchronization for a co-resident (cooperative) grid with a monotonic arrival counter
+// (bar[0], zero at launch and never reset): every CTA's thread 0 adds 1 with release semantics after a
+// CTA barrier, then polls with acquire loads until `target` (= grid size x synchronization number)
+// CTAs have arrived. The CTA's writes before the call are visible to every CTA after it. Returns false
+// if this CTA, or any CTA before it, gave up waiting.
+__device__ bool grid_arrive_wait(unsigned* bar, unsigned target, unsigned* status) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g0 = ld_acquire_u32(bar + 1);
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      unsigned polls = 0;
-      while (ld_acquire_u32(bar + 1) == g0) {
-        if ((++polls & 255u) == 0) {
-          if (clock64() - t0 > kBarrierCycles) {
-            atomicOr(status, kStatusTimeout);
-            break;
-          }
-          // Another CTA already gave up: stop waiting.
-          if (*(volatile unsigned*)status & kStatusTimeout) break;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    const long long t0 = clock64();
+    unsigned polls = 0;
+    while (ld_acquire_u32(bar) < target) {
+      if ((++polls & 255u) == 0) {
+        if (clock64() - t0 > kBarrierCycles) {
+          atomicOr(status, kStatusTimeout);
+          break;
         }
-        if (polls > 512) __nanosleep(32);
+        // Another CTA already gave up: stop waiting.
+        if (*(volatile unsigned*)status & kStatusTimeout) break;
       }
+      if (polls > 512) __nanosleep(32);
     }
-    __threadfence();
     ok = (*(volatile unsigned*)status & kStatusTimeout) == 0;
   }
   __syncthreads();
@@ -147,20 +141,14 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
       const int64_t rl = j - row0;
       for (int64_t c = j + threadIdx.x; c <= n; c += blockDim.x) L.R[j * ldw + c] = Wl[rl * ldw + c];
     }
-    if (!grid_barrier(L.bar, nb, L.status)) return;
-    // Reflector: alpha = -sign(x0) ||x||, v_j = x0 - alpha, tau = 2 / v^T v.
-    if (threadIdx.x == 0) {
-      const double norm2 = __ldcg(&a.nrm[j]);
-      const double x0 = __ldcg(&L.R[j * ldw + j]);
-      const double alpha = -copysign(sqrt(norm2), x0);
-      const double vj = x0 - alpha;
-      const double vtv = (norm2 - x0 * x0) + vj * vj;
-      sc[0] = alpha;
-      sc[1] = vj;
-      sc[2] = (vtv > 0.0) ? 2.0 / vtv : 0.0;
-    }
-    __syncthreads();
-    const double alpha = sc[0], vj = sc[1], tau = sc[2];
+    if (!grid_arrive_wait(L.bar, nb * (unsigned)(j + 1), L.status)) return;
+    // Reflector (every thread): alpha = -sign(x0) ||x||, v_j = x0 - alpha, tau = 2 / v^T v.
+    const double norm2 = __ldcg(&a.nrm[j]);
+    const double x0 = __ldcg(&L.R[j * ldw + j]);
+    const double alpha = -copysign(sqrt(norm2), x0);
+    const double vj = x0 - alpha;
+    const double vtv = (norm2 - x0 * x0) + vj * vj;
+    const double tau = (vtv > 0.0) ? 2.0 / vtv : 0.0;
     // W[r][c] -= tau v_r w_c with w_c = v^T W[:, c] = x^T W[:, c] - alpha W[j][c] (staged once per CTA).
     if (tau != 0.0) {
       for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x)
@@ -175,20 +163,17 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
         Wl[rl * ldw + c] -= tau * vr * wsm[c];
       }
     }
-    __syncthreads();
-    if (j >= row0 && j < row0 + nown) {
-      const int64_t rl = j - row0;
-      if (threadIdx.x == 0) Wl[rl * ldw + j] = alpha;
-    }
+    // The owner's diagonal becomes alpha (the update above reads column j only below the diagonal).
+    if (threadIdx.x == 0 && j >= row0 && j < row0 + nown) Wl[(j - row0) * ldw + j] = alpha;
     __syncthreads();
   }
   // Final R rows: each owner rewrites its rows of R (diagonal alpha, updated off-diagonals).
-  if (!grid_barrier(L.bar, nb, L.status)) return;
+  if (!grid_arrive_wait(L.bar, nb * (unsigned)(n + 1), L.status)) return;
   for (int64_t jr = row0; jr < row0 + nown && jr < n; ++jr) {
     const int64_t rl = jr - row0;
     for (int64_t c = jr + threadIdx.x; c <= n; c += blockDim.x) L.R[jr * ldw + c] = Wl[rl * ldw + c];
   }
-  if (!grid_barrier(L.bar, nb, L.status)) return;
+  if (!grid_arrive_wait(L.bar, nb * (unsigned)(n + 2), L.status)) return;
   if (b != 0) return;
   // Back substitution on CTA 0 (column-oriented): rhs in shared memory (reuses Wl).
   double* rhs = Wl;
