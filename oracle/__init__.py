@@ -10,7 +10,8 @@ at the bottom use numpy's FP64 QR/SVD as library steps.
 
 Sources restated (see the C file for the per-function citations):
   * SparseStack operator, paper Sec. 2.2 (Definition of SparseStack) and Sec. 4.1.
-  * FP16 quantizers, paper Sec. 4.2 (round-to-nearest, exact stochastic, dithered).
+  * FP16 quantizers, paper Sec. 4.2 (round-to-nearest, exact stochastic, dithered), and the
+    bfloat16 round-to-nearest rule (Sec. 4.2 names BF16 beside FP16 as a 16-bit reduction target).
   * Distortion eta(S, U), paper Sec. 2.2 / Sec. 5.1.
   * Sketch-and-solve least squares, paper Sec. 5.1 (min ||SAx - Sb||).
 """
@@ -29,8 +30,8 @@ _LIB_PATH = os.path.join(_HERE, "libsk_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FP32, FP16_RN, FP16_SR, FP16_DITHER = 0, 1, 2, 3
-RULES = {"fp32": FP32, "fp16_rn": FP16_RN, "fp16_sr": FP16_SR, "fp16_dither": FP16_DITHER}
+FP32, FP16_RN, FP16_SR, FP16_DITHER, BF16_RN = 0, 1, 2, 3, 4
+RULES = {"fp32": FP32, "fp16_rn": FP16_RN, "fp16_sr": FP16_SR, "fp16_dither": FP16_DITHER, "bf16_rn": BF16_RN}
 
 
 def build(force: bool = False) -> str:
@@ -67,6 +68,12 @@ def lib():
             L.sko_round_to_half.argtypes = [ctypes.c_double, ctypes.c_int]
             L.sko_half_add.restype = u16
             L.sko_half_add.argtypes = [u16, u16]
+            L.sko_bf16_to_double.restype = ctypes.c_double
+            L.sko_bf16_to_double.argtypes = [u16]
+            L.sko_round_to_bf16.restype = u16
+            L.sko_round_to_bf16.argtypes = [ctypes.c_double]
+            L.sko_bf16_add.restype = u16
+            L.sko_bf16_add.argtypes = [u16, u16]
             L.sko_quantize.restype = u16
             L.sko_quantize.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int]
             L.sko_sketch_f64.restype = None
@@ -148,6 +155,28 @@ def half_add(a: int, b: int) -> int:
     return int(lib().sko_half_add(a & 0xFFFF, b & 0xFFFF))
 
 
+def bf16_to_double(h: int) -> float:
+    return float(lib().sko_bf16_to_double(h & 0xFFFF))
+
+
+def round_to_bf16(x: float) -> int:
+    return int(lib().sko_round_to_bf16(float(x)))
+
+
+def bf16_add(a: int, b: int) -> int:
+    return int(lib().sko_bf16_add(a & 0xFFFF, b & 0xFFFF))
+
+
+def bf16bits_to_f64(h: np.ndarray) -> np.ndarray:
+    """bfloat16 bit patterns (uint16) to float64, exactly."""
+    return (np.asarray(h, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def bits16_to_f64(h: np.ndarray, rule: int) -> np.ndarray:
+    """16-bit results of an FP16 or BF16 rule to float64."""
+    return bf16bits_to_f64(h) if rule == BF16_RN else halfbits_to_f64(h)
+
+
 def quantize(x: float, u: float, rule: int) -> int:
     return int(lib().sko_quantize(np.float32(x), np.float32(u), rule))
 
@@ -166,7 +195,7 @@ def sketch_f64(A: np.ndarray, d: int, k: int, seed: int) -> np.ndarray:
 
 
 def sketch_canonical(A: np.ndarray, d: int, k: int, seed: int, rule: int, R: int) -> np.ndarray:
-    """Canonical-order result: float32 (rule FP32) or binary16 bits as uint16."""
+    """Canonical-order result: float32 (rule FP32) or the 16-bit patterns (binary16 or bfloat16) as uint16."""
     if d % k != 0 or R < 1:
         raise ValueError("need d % k == 0 and R >= 1")
     A, lda = _as_f32_rows(A)
@@ -189,7 +218,7 @@ def sketch_sampled(A: np.ndarray, d: int, k: int, seed: int, rule: int, R: int, 
     if rule == FP32:
         canon = outc.view(np.float32).astype(np.float64)
     else:
-        canon = halfbits_to_f64(outc.astype(np.uint16))
+        canon = bits16_to_f64(outc.astype(np.uint16), rule)
     return out64, canon
 
 

@@ -192,8 +192,71 @@ SKO_EXPORT uint16_t sko_half_add(uint16_t a, uint16_t b) {
   return sko_round_to_half(sko_half_to_double(a) + sko_half_to_double(b), 0);
 }
 
+/* ---------------------------------------------------------------- bfloat16 */
+/* bfloat16 (paper Sec. 4.2 names it beside FP16 as a 16-bit reduction target): the upper 16 bits of
+ * a binary32, i.e. 8 significant bits with binary32's exponent range. */
+
+/* Exact value of a bfloat16 bit pattern as a double. */
+SKO_EXPORT double sko_bf16_to_double(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+/* Round a double to bfloat16, nearest with ties to even (same construction as sko_round_to_half:
+ * scale by the quantum of the binade, round the integer part, scale back). */
+SKO_EXPORT uint16_t sko_round_to_bf16(double x) {
+  if (isnan(x)) return 0x7FC0u;
+  uint16_t sgn = signbit(x) ? 0x8000u : 0u;
+  double a = fabs(x);
+  if (a == 0.0) return sgn;
+  if (isinf(a)) return (uint16_t)(sgn | 0x7F80u);
+  int E2;
+  (void)frexp(a, &E2);
+  int e = E2 - 1;                         /* a in [2^e, 2^(e+1)) */
+  if (e > 127) return (uint16_t)(sgn | 0x7F80u);
+  int qexp = (e < -126) ? -133 : (e - 7); /* quantum: 7 fraction bits, subnormal quantum 2^-133 */
+  double N = ldexp(a, -qexp);
+  double nf = floor(N);
+  double frac = N - nf;
+  double n = nf;
+  if (frac > 0.5) n = nf + 1.0;
+  else if (frac == 0.5) n = (fmod(nf, 2.0) == 0.0) ? nf : nf + 1.0;
+  double M = ldexp(n, qexp);
+  if (M == 0.0) return sgn;
+  if (M >= 0x1p128) return (uint16_t)(sgn | 0x7F80u);
+  int E2m;
+  (void)frexp(M, &E2m);
+  int em = E2m - 1;
+  uint16_t bits;
+  if (em < -126) {
+    bits = (uint16_t)ldexp(M, 133); /* subnormal: M = bits * 2^-133 */
+  } else {
+    uint32_t mant = (uint32_t)ldexp(M, 7 - em) - 128u;
+    bits = (uint16_t)(((uint32_t)(em + 127) << 7) | mant);
+  }
+  return (uint16_t)(sgn | bits);
+}
+
+/* bfloat16 + bfloat16, rounded to nearest even. The double sum is exact unless the exponents differ
+ * by more than 45; then the smaller operand is far below half an ulp of the larger, and the exact
+ * and the double sum both round to the larger operand, so one rounding of the double sum is the
+ * correctly rounded result. */
+SKO_EXPORT uint16_t sko_bf16_add(uint16_t a, uint16_t b) {
+  return sko_round_to_bf16(sko_bf16_to_double(a) + sko_bf16_to_double(b));
+}
+
 /* ---------------------------------------------------------------- quantizers (paper Sec. 4.2) */
-enum { SKO_FP32 = 0, SKO_FP16_RN = 1, SKO_FP16_SR = 2, SKO_FP16_DITHER = 3 };
+enum { SKO_FP32 = 0, SKO_FP16_RN = 1, SKO_FP16_SR = 2, SKO_FP16_DITHER = 3, SKO_BF16_RN = 4 };
+
+/* 16-bit addition of the rule's format (binary16 or bfloat16), round to nearest even. */
+static uint16_t sko_add16(uint16_t a, uint16_t b, int rule) {
+  return (rule == SKO_BF16_RN) ? sko_bf16_add(a, b) : sko_half_add(a, b);
+}
+
+/* Rules that draw no random bits. */
+static int sko_rule_is_rn(int rule) { return rule == SKO_FP16_RN || rule == SKO_BF16_RN; }
 
 /* x: the FP32 value to store; u: uniform in [0,1). Every FP32 operation rounds (no contraction). */
 SKO_EXPORT uint16_t sko_quantize(float x, float u, int rule) {
@@ -209,6 +272,9 @@ SKO_EXPORT uint16_t sko_quantize(float x, float u, int rule) {
     float dist_exact = x - frd;
     float prod = u * dist_total;
     return (prod < dist_exact) ? ru : rd;
+  }
+  if (rule == SKO_BF16_RN) {
+    return sko_round_to_bf16((double)x);
   }
   if (rule == SKO_FP16_DITHER) {
     const float ulp_scale = 1.0f / 1024.0f; /* 2^-10 */
@@ -248,8 +314,9 @@ SKO_EXPORT void sko_sketch_f64(const float* A, int64_t lda, int64_t m, int64_t n
  * s_ij = r, in ascending t: P = FP32 sum from +0 of sign*A[i,c] over those rows in ascending i;
  * x = fl32(scale * P) with scale = fl32(1/sqrt(k)); then
  *   FP32 rule:  Y = fl32(Y + x);
- *   FP16 rules: Y = RN16(Y + Q(x, u(r, c, t))).
- * Y starts at +0. Y is float[d*n] for the FP32 rule, binary16 bits uint16[d*n] otherwise. */
+ *   FP16 rules: Y = RN16(Y + Q(x, u(r, c, t)));
+ *   BF16 rule:  Y = RNbf16(Y + RNbf16(x)).
+ * Y starts at +0. Y is float[d*n] for the FP32 rule, 16-bit patterns uint16[d*n] otherwise. */
 SKO_EXPORT void sko_sketch_canonical(const float* A, int64_t lda, int64_t m, int64_t n, int64_t d, int32_t k,
                                      uint64_t seed, int rule, int64_t R, void* Yout) {
   int64_t B = d / k;
@@ -297,9 +364,9 @@ SKO_EXPORT void sko_sketch_canonical(const float* A, int64_t lda, int64_t m, int
           if (rule == SKO_FP32) {
             Y32[r * n + c] = Y32[r * n + c] + x;
           } else {
-            float u = (rule == SKO_FP16_RN) ? 0.0f : sko_uniform(seed, r, c, t);
+            float u = sko_rule_is_rn(rule) ? 0.0f : sko_uniform(seed, r, c, t);
             uint16_t qv = sko_quantize(x, u, rule);
-            Y16[r * n + c] = sko_half_add(Y16[r * n + c], qv);
+            Y16[r * n + c] = sko_add16(Y16[r * n + c], qv, rule);
           }
           touched[sl] = 0;
         }
@@ -314,7 +381,7 @@ SKO_EXPORT void sko_sketch_canonical(const float* A, int64_t lda, int64_t m, int
 }
 
 /* The same two results at selected outputs only, for matrices too large for the full oracle.
- * out64[q] = FP64 value and outc[q] = canonical value (float, or binary16 bits in the low 16 bits
+ * out64[q] = FP64 value and outc[q] = canonical value (float, or the 16-bit pattern in the low 16 bits
  * of a uint32) at output (rs[q], cs[q]). Every row of A is scanned once per selected output. */
 SKO_EXPORT void sko_sketch_sampled(const float* A, int64_t lda, int64_t m, int64_t n, int64_t d, int32_t k,
                                    uint64_t seed, int rule, int64_t R, int64_t cnt, const int64_t* rs,
@@ -346,8 +413,8 @@ SKO_EXPORT void sko_sketch_sampled(const float* A, int64_t lda, int64_t m, int64
           if (rule == SKO_FP32) {
             Y32 = Y32 + x;
           } else {
-            float u = (rule == SKO_FP16_RN) ? 0.0f : sko_uniform(seed, r, c, cur_t);
-            Y16 = sko_half_add(Y16, sko_quantize(x, u, rule));
+            float u = sko_rule_is_rn(rule) ? 0.0f : sko_uniform(seed, r, c, cur_t);
+            Y16 = sko_add16(Y16, sko_quantize(x, u, rule), rule);
           }
         }
         cur_t = t;
@@ -360,8 +427,8 @@ SKO_EXPORT void sko_sketch_sampled(const float* A, int64_t lda, int64_t m, int64
       if (rule == SKO_FP32) {
         Y32 = Y32 + x;
       } else {
-        float u = (rule == SKO_FP16_RN) ? 0.0f : sko_uniform(seed, r, c, cur_t);
-        Y16 = sko_half_add(Y16, sko_quantize(x, u, rule));
+        float u = sko_rule_is_rn(rule) ? 0.0f : sko_uniform(seed, r, c, cur_t);
+        Y16 = sko_add16(Y16, sko_quantize(x, u, rule), rule);
       }
     }
     out64[q] = acc64 * inv;
