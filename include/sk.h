@@ -53,7 +53,8 @@ typedef enum {
   SK_FP32 = 0,       /* Y is float; contributions added in FP32 */
   SK_FP16_RN = 1,    /* Y is binary16; each contribution rounded to nearest even */
   SK_FP16_SR = 2,    /* Y is binary16; exact stochastic rounding of each contribution */
-  SK_FP16_DITHER = 3 /* Y is binary16; uniform dither of ~1 binary16 ulp, then nearest even */
+  SK_FP16_DITHER = 3, /* Y is binary16; uniform dither of ~1 binary16 ulp, then nearest even */
+  SK_BF16_RN = 4      /* Y is bfloat16; each contribution rounded to nearest even, bfloat16 adds */
 } sk_rule;
 
 /* Plan parameters for sk_plan_set / sk_plan_get. */

@@ -475,7 +475,7 @@ sk_status sk_plan_create(int64_t d, int64_t m, int32_t k, int32_t rule, uint64_t
   if (d > 0x7fffffffLL) return set_error(SK_ERR_UNSUPPORTED, "d=%lld above 2^31-1", (long long)d);
   if (m < 1) return set_error(SK_ERR_INVALID_ARG, "m=%lld must be >= 1", (long long)m);
   if (m > ((int64_t)1 << 56)) return set_error(SK_ERR_UNSUPPORTED, "m=%lld too large", (long long)m);
-  if (rule < SK_FP32 || rule > SK_FP16_DITHER) return set_error(SK_ERR_INVALID_ARG, "unknown rule %d", rule);
+  if (rule < SK_FP32 || rule > SK_BF16_RN) return set_error(SK_ERR_INVALID_ARG, "unknown rule %d", rule);
   sk_plan_s* p = new (std::nothrow) sk_plan_s();
   if (!p) return set_error(SK_ERR_OOM, "host allocation failed");
   p->d = d;

@@ -96,6 +96,7 @@ static const void* batch_kernel_ptr(int rule) {
     case kRN: return (const void*)batch_kernel<kRN>;
     case kSR: return (const void*)batch_kernel<kSR>;
     case kDither: return (const void*)batch_kernel<kDither>;
+    case kBF16: return (const void*)batch_kernel<kBF16>;
     default: return (const void*)batch_kernel<kFP32>;
   }
 }
@@ -117,6 +118,7 @@ cudaError_t launch_batch(const void* descs, const void* work, int64_t nwork, int
     case kRN: batch_kernel<kRN><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
     case kSR: batch_kernel<kSR><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
     case kDither: batch_kernel<kDither><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
+    case kBF16: batch_kernel<kBF16><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
     default: batch_kernel<kFP32><<<grid, threads, smem, st>>>(dd, ww, nwork, counter, acc_floats, slot_bytes, depth, status); break;
   }
   if (launches) *launches += 1;
@@ -366,7 +368,7 @@ sk_status sk_batch_create(const sk_batch_item* items, int32_t count, int32_t rul
   if (!out) return set_error(SK_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!items || count < 1) return set_error(SK_ERR_INVALID_ARG, "need at least one item");
-  if (rule < SK_FP32 || rule > SK_FP16_DITHER) return set_error(SK_ERR_INVALID_ARG, "unknown rule %d", rule);
+  if (rule < SK_FP32 || rule > SK_BF16_RN) return set_error(SK_ERR_INVALID_ARG, "unknown rule %d", rule);
   for (int32_t i = 0; i < count; ++i) {
     const sk_batch_item& it = items[i];
     if (!it.A_dev || !it.Y_dev) return set_error(SK_ERR_INVALID_ARG, "item %d: NULL pointer", i);

@@ -6,6 +6,7 @@
 // bit for bit.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
 
@@ -84,7 +85,7 @@ __device__ __forceinline__ void uniforms4(uint64_t seed, uint32_t r, uint32_t q,
 }
 
 // ------------------------------------------------------------------ FP16 quantizers (paper Sec. 4.2)
-enum Rule : int { kFP32 = 0, kRN = 1, kSR = 2, kDither = 3 };
+enum Rule : int { kFP32 = 0, kRN = 1, kSR = 2, kDither = 3, kBF16 = 4 };
 
 // Exact stochastic rounding: upper neighbour with probability (x - rd) / (ru - rd).
 __device__ __forceinline__ __half quant_sr(float x, float u) {
@@ -108,6 +109,46 @@ __device__ __forceinline__ __half quantize(float x, float u) {
   if (RULE == kSR) return quant_sr(x, u);
   if (RULE == kDither) return quant_dither(x, u);
   return __float2half_rn(x);
+}
+
+// ------------------------------------------------------------------ 16-bit rules as bit patterns
+// The 16-bit rules store Y as binary16 (FP16 rules) or bfloat16 (kBF16: round to nearest even, the
+// BF16 reduction target of paper Sec. 4.2). Values travel as their 16-bit patterns.
+
+// Rules whose quantizer draws uniforms (the others round to nearest).
+template <int RULE>
+__device__ __forceinline__ constexpr bool rule_draws_bits() {
+  return RULE == kSR || RULE == kDither;
+}
+
+template <int RULE>
+__device__ __forceinline__ uint16_t quantize16(float x, float u) {
+  if (RULE == kBF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+  return __half_as_ushort(quantize<RULE>(x, u));
+}
+
+// a + b in the rule's 16-bit format, rounded to nearest even.
+template <int RULE>
+__device__ __forceinline__ uint16_t add16(uint16_t a, uint16_t b) {
+  if (RULE == kBF16) return __bfloat16_as_ushort(__hadd(__ushort_as_bfloat16(a), __ushort_as_bfloat16(b)));
+  return __half_as_ushort(__hadd(__ushort_as_half(a), __ushort_as_half(b)));
+}
+
+// Atomic y[0] += q0, y[1] += q1 (one packed 32-bit atomic; y 4-byte aligned), and the scalar form.
+template <int RULE>
+__device__ __forceinline__ void atomic_add16x2(uint16_t* y, uint16_t q0, uint16_t q1) {
+  if (RULE == kBF16) {
+    atomicAdd(reinterpret_cast<__nv_bfloat162*>(y),
+              __halves2bfloat162(__ushort_as_bfloat16(q0), __ushort_as_bfloat16(q1)));
+  } else {
+    atomicAdd(reinterpret_cast<__half2*>(y), __halves2half2(__ushort_as_half(q0), __ushort_as_half(q1)));
+  }
+}
+
+template <int RULE>
+__device__ __forceinline__ void atomic_add16(uint16_t* y, uint16_t q) {
+  if (RULE == kBF16) atomicAdd(reinterpret_cast<__nv_bfloat16*>(y), __ushort_as_bfloat16(q));
+  else atomicAdd(reinterpret_cast<__half*>(y), __ushort_as_half(q));
 }
 
 // Status word bits written by kernels that detect a problem (never trap).

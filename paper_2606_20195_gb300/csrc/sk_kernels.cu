@@ -273,6 +273,7 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
     case kRN: kern = tile_kernel<kRN>; break;
     case kSR: kern = tile_kernel<kSR>; break;
     case kDither: kern = tile_kernel<kDither>; break;
+    case kBF16: kern = tile_kernel<kBF16>; break;
     default: kern = tile_kernel<kFP32>; break;
   }
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -313,6 +314,7 @@ cudaError_t launch_chunk_finish(const TileDesc& D, int32_t rule, float* P, int64
     case kRN: chunk_finish_kernel<kRN><<<grid, 256, 0, st>>>(D, P, t_first, chunks); break;
     case kSR: chunk_finish_kernel<kSR><<<grid, 256, 0, st>>>(D, P, t_first, chunks); break;
     case kDither: chunk_finish_kernel<kDither><<<grid, 256, 0, st>>>(D, P, t_first, chunks); break;
+    case kBF16: chunk_finish_kernel<kBF16><<<grid, 256, 0, st>>>(D, P, t_first, chunks); break;
     default: chunk_finish_kernel<kFP32><<<grid, 256, 0, st>>>(D, P, t_first, chunks); break;
   }
   if (launches) *launches += 1;
@@ -325,6 +327,7 @@ int32_t tile_ctas_per_sm(int32_t rule, int32_t threads, size_t smem) {
     case kRN: kern = tile_kernel<kRN>; break;
     case kSR: kern = tile_kernel<kSR>; break;
     case kDither: kern = tile_kernel<kDither>; break;
+    case kBF16: kern = tile_kernel<kBF16>; break;
     default: kern = tile_kernel<kFP32>; break;
   }
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -373,22 +376,22 @@ __global__ void literal_kernel(const LiteralLaunch L, uint32_t B, uint32_t kp) {
       } else {
         float u[4] = {0.f, 0.f, 0.f, 0.f}, u1n[4] = {0.f, 0.f, 0.f, 0.f};
         const int64_t cg = L.col_off + c0;
-        if (RULE != kRN) {
+        if (rule_draws_bits<RULE>()) {
           uniforms4(L.seed, r, (uint32_t)(cg >> 2), (uint64_t)i, u);
           if ((cg & 3) == 3 && has1) uniforms4(L.seed, r, (uint32_t)(cg >> 2) + 1u, (uint64_t)i, u1n);
         }
-        const __half q0 = quantize<RULE>(x0, u[cg & 3]);
-        __half* y = reinterpret_cast<__half*>(L.Y) + (int64_t)r * n + c0;
+        const uint16_t q0 = quantize16<RULE>(x0, u[cg & 3]);
+        uint16_t* y = reinterpret_cast<uint16_t*>(L.Y) + (int64_t)r * n + c0;
         if (has1) {
-          const __half q1 = quantize<RULE>(x1, ((cg & 3) == 3) ? u1n[0] : u[(cg + 1) & 3]);
+          const uint16_t q1 = quantize16<RULE>(x1, ((cg & 3) == 3) ? u1n[0] : u[(cg + 1) & 3]);
           if (even) {
-            atomicAdd(reinterpret_cast<__half2*>(y), __halves2half2(q0, q1));
+            atomic_add16x2<RULE>(y, q0, q1);
           } else {
-            atomicAdd(y, q0);
-            atomicAdd(y + 1, q1);
+            atomic_add16<RULE>(y, q0);
+            atomic_add16<RULE>(y + 1, q1);
           }
         } else {
-          atomicAdd(y, q0);
+          atomic_add16<RULE>(y, q0);
         }
       }
     }
@@ -409,6 +412,7 @@ cudaError_t launch_literal(const LiteralLaunch& L, cudaStream_t st, int32_t* lau
     case kRN: literal_kernel<kRN><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
     case kSR: literal_kernel<kSR><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
     case kDither: literal_kernel<kDither><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
+    case kBF16: literal_kernel<kBF16><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
     default: literal_kernel<kFP32><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
   }
   if (launches) *launches += 1;
@@ -452,9 +456,9 @@ __global__ void det_kernel(const DetLaunch L, uint32_t B, uint32_t kp) {
       } else {
         float u[4] = {0.f, 0.f, 0.f, 0.f};
         const int64_t cg = L.col_off + c;
-        if (RULE != kRN) uniforms4(L.seed, (uint32_t)r, (uint32_t)(cg >> 2), (uint64_t)t, u);
-        __half* y = reinterpret_cast<__half*>(L.Y) + r * n + c;
-        *y = __hadd(*y, quantize<RULE>(x, u[cg & 3]));
+        if (rule_draws_bits<RULE>()) uniforms4(L.seed, (uint32_t)r, (uint32_t)(cg >> 2), (uint64_t)t, u);
+        uint16_t* y = reinterpret_cast<uint16_t*>(L.Y) + r * n + c;
+        *y = add16<RULE>(*y, quantize16<RULE>(x, u[cg & 3]));
       }
     }
   }
@@ -472,6 +476,7 @@ cudaError_t launch_det(const DetLaunch& L, cudaStream_t st, int32_t* launches) {
     case kRN: det_kernel<kRN><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
     case kSR: det_kernel<kSR><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
     case kDither: det_kernel<kDither><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
+    case kBF16: det_kernel<kBF16><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
     default: det_kernel<kFP32><<<(unsigned)grid, threads, 0, st>>>(L, B, kp); break;
   }
   if (launches) *launches += 1;

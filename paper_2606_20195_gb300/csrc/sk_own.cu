@@ -209,6 +209,7 @@ OwnKernel own_kernel_ptr(int32_t rule) {
     case kRN: return own_kernel<kRN>;
     case kSR: return own_kernel<kSR>;
     case kDither: return own_kernel<kDither>;
+    case kBF16: return own_kernel<kBF16>;
     default: return own_kernel<kFP32>;
   }
 }

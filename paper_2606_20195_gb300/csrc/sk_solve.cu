@@ -13,9 +13,11 @@
 // Every grid synchronization waits at most about two seconds: on expiry the kernel sets
 // kStatusTimeout in the status word and all CTAs leave at the next check, so a stalled launch cannot
 // hang the GPU.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "sk_device.cuh"
 #include "sk_internal.h"
@@ -93,7 +95,9 @@ struct QRArgs {
 
 template <typename T>
 __device__ __forceinline__ double load_val(const void* p, int64_t idx) {
-  if constexpr (sizeof(T) == 2) return (double)__half2float(reinterpret_cast<const __half*>(p)[idx]);
+  if constexpr (std::is_same<T, __half>::value) return (double)__half2float(reinterpret_cast<const __half*>(p)[idx]);
+  else if constexpr (std::is_same<T, __nv_bfloat16>::value)
+    return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[idx]);
   else return (double)reinterpret_cast<const float*>(p)[idx];
 }
 
@@ -235,7 +239,9 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launche
   if (e != cudaSuccess) return e;
   const size_t smem = std::max<size_t>((size_t)a.rpc * (size_t)(L.n + 1) * 8, (size_t)L.n * 8);
   void* args[] = {(void*)&a};
-  const void* kern = (L.rule == kFP32) ? (const void*)qr64_kernel<float> : (const void*)qr64_kernel<__half>;
+  const void* kern = (L.rule == kFP32)   ? (const void*)qr64_kernel<float>
+                     : (L.rule == kBF16) ? (const void*)qr64_kernel<__nv_bfloat16>
+                                         : (const void*)qr64_kernel<__half>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)L.ncta), dim3(256), args, smem, st);

@@ -565,14 +565,14 @@ __device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int6
 // (paper Sec. 4.2).
 template <int RULE>
 __device__ __forceinline__ void scale_quad(const TileDesc& D, uint32_t r, int64_t col0, float4 v, int64_t t, float x[4],
-                                           __half q[4]) {
+                                           uint16_t q[4]) {
   x[0] = __fmul_rn(D.scale, v.x);
   x[1] = __fmul_rn(D.scale, v.y);
   x[2] = __fmul_rn(D.scale, v.z);
   x[3] = __fmul_rn(D.scale, v.w);
   if (RULE != kFP32) {
     float u[4] = {0.f, 0.f, 0.f, 0.f};
-    if (RULE != kRN) {
+    if (rule_draws_bits<RULE>()) {
       // Columns col_off + col0 .. +3 of the global column space; their uniforms come from at most
       // two Philox calls (words (column mod 4) of counter column quad floor(column / 4)).
       const int64_t cg = D.col_off + col0;
@@ -588,7 +588,7 @@ __device__ __forceinline__ void scale_quad(const TileDesc& D, uint32_t r, int64_
       }
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) q[e] = quantize<RULE>(x[e], u[e]);
+    for (int e = 0; e < 4; ++e) q[e] = quantize16<RULE>(x[e], u[e]);
   }
 }
 
@@ -598,7 +598,7 @@ template <int RULE>
 __device__ __forceinline__ void emit_quad(const TileDesc& D, uint32_t r, int64_t col0, float4 v, int64_t t) {
   const int64_t n = D.n;
   float x[4];
-  __half q[4];
+  uint16_t q[4];
   scale_quad<RULE>(D, r, col0, v, t, x, q);
   if (RULE == kFP32) {
     float* y = reinterpret_cast<float*>(D.Y) + (int64_t)r * n + col0;
@@ -613,15 +613,15 @@ __device__ __forceinline__ void emit_quad(const TileDesc& D, uint32_t r, int64_t
       if (col0 + 3 < n) atomicAdd(y + 3, x[3]);
     }
   } else {
-    __half* y = reinterpret_cast<__half*>(D.Y) + (int64_t)r * n + col0;
+    uint16_t* y = reinterpret_cast<uint16_t*>(D.Y) + (int64_t)r * n + col0;
     if ((n & 1) == 0) {
-      atomicAdd(reinterpret_cast<__half2*>(y), __halves2half2(q[0], q[1]));  // col0 + 1 < n since n even
-      if (col0 + 3 < n) atomicAdd(reinterpret_cast<__half2*>(y + 2), __halves2half2(q[2], q[3]));
+      atomic_add16x2<RULE>(y, q[0], q[1]);  // col0 + 1 < n since n even
+      if (col0 + 3 < n) atomic_add16x2<RULE>(y + 2, q[2], q[3]);
     } else {
-      atomicAdd(y, q[0]);
-      if (col0 + 1 < n) atomicAdd(y + 1, q[1]);
-      if (col0 + 2 < n) atomicAdd(y + 2, q[2]);
-      if (col0 + 3 < n) atomicAdd(y + 3, q[3]);
+      atomic_add16<RULE>(y, q[0]);
+      if (col0 + 1 < n) atomic_add16<RULE>(y + 1, q[1]);
+      if (col0 + 2 < n) atomic_add16<RULE>(y + 2, q[2]);
+      if (col0 + 3 < n) atomic_add16<RULE>(y + 3, q[3]);
     }
   }
 }
@@ -638,7 +638,7 @@ __device__ __forceinline__ void finish_quad(const TileDesc& D, uint32_t r, int64
   const bool vec = (n & 3) == 0;
   const int64_t off = (int64_t)r * n + col0;
   float yf[4] = {0.f, 0.f, 0.f, 0.f};
-  __half yh[4];
+  uint16_t yh[4] = {0, 0, 0, 0};
   bool loaded = false, touched = false;
   for (int64_t tl = 0; tl < chunks; ++tl) {
     float* p = P + tl * dn + off;
@@ -663,18 +663,18 @@ __device__ __forceinline__ void finish_quad(const TileDesc& D, uint32_t r, int64
         const float* y = reinterpret_cast<const float*>(D.Y) + off;
         for (int e = 0; e < ne; ++e) yf[e] = y[e];
       } else {
-        const __half* y = reinterpret_cast<const __half*>(D.Y) + off;
+        const uint16_t* y = reinterpret_cast<const uint16_t*>(D.Y) + off;
         for (int e = 0; e < ne; ++e) yh[e] = y[e];
       }
     }
     float x[4];
-    __half q[4];
+    uint16_t q[4];
     scale_quad<RULE>(D, r, col0, v, t_first + tl, x, q);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (e < ne) {
         if (RULE == kFP32) yf[e] = __fadd_rn(yf[e], x[e]);
-        else yh[e] = __hadd(yh[e], q[e]);
+        else yh[e] = add16<RULE>(yh[e], q[e]);
       }
     }
     touched = true;
@@ -684,7 +684,7 @@ __device__ __forceinline__ void finish_quad(const TileDesc& D, uint32_t r, int64
     float* y = reinterpret_cast<float*>(D.Y) + off;
     for (int e = 0; e < ne; ++e) y[e] = yf[e];
   } else {
-    __half* y = reinterpret_cast<__half*>(D.Y) + off;
+    uint16_t* y = reinterpret_cast<uint16_t*>(D.Y) + off;
     for (int e = 0; e < ne; ++e) y[e] = yh[e];
   }
 }

@@ -13,8 +13,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsk.so")
 
 SK_OK, SK_ERR_INVALID_ARG, SK_ERR_UNSUPPORTED, SK_ERR_OOM, SK_ERR_CUDA, SK_ERR_TIMEOUT, SK_ERR_NUMERIC = range(7)
-SK_FP32, SK_FP16_RN, SK_FP16_SR, SK_FP16_DITHER = range(4)
-RULES = {"fp32": SK_FP32, "fp16_rn": SK_FP16_RN, "fp16_sr": SK_FP16_SR, "fp16_dither": SK_FP16_DITHER}
+SK_FP32, SK_FP16_RN, SK_FP16_SR, SK_FP16_DITHER, SK_BF16_RN = range(5)
+RULES = {"fp32": SK_FP32, "fp16_rn": SK_FP16_RN, "fp16_sr": SK_FP16_SR, "fp16_dither": SK_FP16_DITHER,
+         "bf16_rn": SK_BF16_RN}
 SK_PARAM_CHUNK_ROWS, SK_PARAM_MODE, SK_PARAM_ROW_OFFSET, SK_PARAM_KERNEL = 1, 2, 3, 4
 SK_PARAM_TILE_COLS, SK_PARAM_THREADS, SK_PARAM_LAST_LAUNCHES, SK_PARAM_LAST_CHUNK_ROWS = 5, 6, 7, 8
 SK_PARAM_DEVICE_STATUS, SK_PARAM_LAST_KERNEL = 9, 10
@@ -231,7 +232,9 @@ class Plan:
 
     def out_dtype(self):
         import torch
-        return torch.float32 if self.rule == SK_FP32 else torch.float16
+        if self.rule == SK_FP32:
+            return torch.float32
+        return torch.bfloat16 if self.rule == SK_BF16_RN else torch.float16
 
     def apply(self, A, Y=None, stream=None):
         import torch

@@ -15,8 +15,8 @@ from paper_2606_20195_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-RULES = [0, 1, 2, 3]
-TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3}
+RULES = [0, 1, 2, 3, 4]  # FP32, the three FP16 rules and bfloat16 round-to-nearest
+TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3, 4: 2e-2}
 
 
 def _run(sk, A_h, d, k, rule, seed, dev, **params):
@@ -25,8 +25,7 @@ def _run(sk, A_h, d, k, rule, seed, dev, **params):
     plan = sk.Plan(d, A_h.shape[0], k, rule, seed, **params)
     Y = plan.apply(A)
     torch.cuda.synchronize()
-    Yc = Y.cpu().numpy()
-    out = Yc if rule == 0 else Yc.view(np.uint16)
+    out = Y.cpu().numpy() if rule == 0 else Y.view(torch.int16).cpu().numpy().view(np.uint16)
     R = plan.get(sk.SK_PARAM_LAST_CHUNK_ROWS)
     assert plan.get(sk.SK_PARAM_DEVICE_STATUS) == 0
     plan.close()
@@ -44,7 +43,7 @@ def _last_kernel(sk, A_h, d, k, dev, **params):
 
 
 def _as64(Yn, rule):
-    return Yn.astype(np.float64) if rule == 0 else oracle.halfbits_to_f64(Yn)
+    return Yn.astype(np.float64) if rule == 0 else oracle.bits16_to_f64(Yn, rule)
 
 
 # One chunk of fewer than 2 * max(4096, 2d) rows is one work item per (pair of blocks, 32 columns):

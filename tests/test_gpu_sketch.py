@@ -13,16 +13,19 @@ from paper_2606_20195_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 RULES = [0, 1, 2, 3]
-TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3}
+RULES5 = [0, 1, 2, 3, 4]  # with the bfloat16 round-to-nearest rule
+TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3, 4: 2e-2}
 
 
 def _to_np(Y, rule):
-    Yc = Y.cpu().numpy()
-    return Yc if rule == 0 else Yc.view(np.uint16)
+    import torch
+    if rule == 0:
+        return Y.cpu().numpy()
+    return Y.view(torch.int16).cpu().numpy().view(np.uint16)
 
 
 def _as64(Yn, rule):
-    return Yn.astype(np.float64) if rule == 0 else oracle.halfbits_to_f64(Yn)
+    return Yn.astype(np.float64) if rule == 0 else oracle.bits16_to_f64(Yn, rule)
 
 
 def _apply(sk, A_h, d, k, rule, seed, dev, **params):
@@ -54,7 +57,7 @@ def test_pattern_bit_exact(sk, dev, d, k):
     plan.close()
 
 
-@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("rule", RULES5)
 @pytest.mark.parametrize("k", [4, 1])
 @pytest.mark.parametrize("R", [1, 256, 4096])
 def test_deterministic_mode_bit_exact(sk, dev, rule, k, R):
@@ -65,7 +68,7 @@ def test_deterministic_mode_bit_exact(sk, dev, rule, k, R):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("rule", RULES5)
 @pytest.mark.parametrize("k,cols", [(4, 8), (4, 16), (4, 32), (1, 32), (8, 4), (8, 8)])
 def test_serial_tile_bit_exact(sk, dev, rule, k, cols):
     # The fast tile kernel run by one warp of one CTA follows the canonical order: bit-exact.
@@ -76,7 +79,7 @@ def test_serial_tile_bit_exact(sk, dev, rule, k, cols):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("rule", RULES5)
 @pytest.mark.parametrize("k", [4, 1])
 def test_atomic_mode_c0_tolerance(sk, dev, rule, k):
     m, n, d, seed = 16384, 16, 256, 0
@@ -91,7 +94,7 @@ def test_atomic_mode_c0_tolerance(sk, dev, rule, k):
     assert oracle.rel_fro(_as64(got, rule), ref) <= TOL[rule]
 
 
-@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("rule", RULES5)
 @pytest.mark.parametrize("shape", [(1, 1, 8, 1), (7, 3, 12, 3), (1000, 1, 64, 8), (4099, 33, 120, 4),
                                    (50001, 5, 512, 2), (3, 2, 64, 64)])
 def test_atomic_mode_ragged_and_edges(sk, dev, rule, shape):
@@ -112,14 +115,14 @@ def test_atomic_mode_ragged_and_edges(sk, dev, rule, shape):
 # (n a multiple of 4 lets A go through TMA and the tile kernel take the lane-row path; n = 13 takes
 # the direct-load path. The owner kernel runs the same cases where it applies, n >= 32.)
 @pytest.mark.parametrize("shape,R,rules", [
-    ((50001, 64, 4096, 8), 50016, RULES),        # the bench geometry (lane-row path, 8 columns per item)
+    ((50001, 64, 4096, 8), 50016, RULES5),       # the bench geometry (lane-row path, 8 columns per item)
     ((50001, 12, 1024, 4), 0, [0, 1, 2]),        # several chunks, one partly filled 16-column tile
     ((50001, 13, 1024, 4), 0, [0, 1, 2]),        # direct loads (row stride not a multiple of 16 bytes)
     ((20000, 40, 4096, 16), 0, [0, 1, 2]),
-    ((30011, 20, 96, 3), 30016, RULES),          # odd k: the last pair has one block
+    ((30011, 20, 96, 3), 30016, RULES5),         # odd k: the last pair has one block
     ((40000, 36, 512, 1), 0, [0, 1, 2]),         # CountSketch
     ((50001, 1, 1024, 4), 0, [0, 1, 2]),         # one column: the vector path
-    ((30011, 1, 96, 3), 30016, RULES),
+    ((30011, 1, 96, 3), 30016, RULES5),
 ])
 @pytest.mark.parametrize("kernel", ["tile", "owner"])
 def test_atomic_mode_exact_on_integer_data(sk, dev, shape, R, rules, kernel):
@@ -153,7 +156,7 @@ def test_lda_and_row_offset(sk, dev, rule):
     plan.close()
 
 
-@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("rule", RULES5)
 def test_literal_kernel(sk, dev, rule):
     # The paper-literal kernel (R = 1, one atomic per element and nonzero) against the FP64
     # sketch; FP16 rules at R = 1 are less accurate (T = k m / d contributions per output), so the

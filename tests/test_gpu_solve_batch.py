@@ -44,7 +44,7 @@ def test_apply_host_matches_device_path(sk, dev, rule, pinned):
     plan.close()
 
 
-@pytest.mark.parametrize("rule", [0, 1, 2, 3])
+@pytest.mark.parametrize("rule", [0, 1, 2, 3, 4])
 def test_sketch_and_solve_matches_oracle(sk, dev, rule):
     import torch
     m, n, d, k = 1 << 18, 32, 512, 8
@@ -62,7 +62,7 @@ def test_sketch_and_solve_matches_oracle(sk, dev, rule):
         # oracle sketch-and-solve from the canonical sketch of [A | b] with the same chunking
         Ab = np.hstack([A_h, b_h[:, None]])
         SAb = oracle.sketch_canonical(Ab, d, k, 11, rule, R)
-        SAb = SAb.astype(np.float64) if rule == 0 else oracle.halfbits_to_f64(SAb)
+        SAb = SAb.astype(np.float64) if rule == 0 else oracle.bits16_to_f64(SAb, rule)
         x_or = oracle.sketch_solve(SAb[:, :n], SAb[:, n])
         ratio_gpu = oracle.residual_norm(A_h, b_h, x_gpu) / r_opt
         ratio_or = oracle.residual_norm(A_h, b_h, x_or) / r_opt
@@ -78,7 +78,7 @@ def test_sketch_and_solve_matches_oracle(sk, dev, rule):
         plan.close()
 
 
-@pytest.mark.parametrize("rule", [0, 1, 2, 3])
+@pytest.mark.parametrize("rule", [0, 1, 2, 3, 4])
 def test_sketch_and_solve_atomic_mode_noisy_problem(sk, dev, rule):
     # b = A x* + 0.1 N(0,1) with incoherent A: the residual ratio measures the sketch, not rounding.
     import torch
@@ -93,7 +93,7 @@ def test_sketch_and_solve_atomic_mode_noisy_problem(sk, dev, rule):
     R = plan.get(sk.SK_PARAM_LAST_CHUNK_ROWS)
     Ab = np.hstack([A_h, b_h[:, None]])
     SAb = oracle.sketch_canonical(Ab, d, k, 13, rule, R)
-    SAb = SAb.astype(np.float64) if rule == 0 else oracle.halfbits_to_f64(SAb)
+    SAb = SAb.astype(np.float64) if rule == 0 else oracle.bits16_to_f64(SAb, rule)
     x_or = oracle.sketch_solve(SAb[:, :n], SAb[:, n])
     ratio_gpu = oracle.residual_norm(A_h, b_h, x.cpu().numpy().astype(np.float64)) / r_opt
     ratio_or = oracle.residual_norm(A_h, b_h, x_or) / r_opt
