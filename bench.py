@@ -2,7 +2,7 @@
 
 Workload (default): the single-matrix sweep configuration m = 2^22, n = 64, d = 4096, k = 8,
 A FP32 iid N(0, 1) (the incoherent family), accumulation FP16 round-to-nearest (the headline rule);
-FP32 / stochastic / dithered variants are timed beside it. A is 1 GiB, larger than the 129 MB L2,
+FP32 / stochastic / dithered / bfloat16 variants are timed beside it. A is 1 GiB, larger than the 129 MB L2,
 so no L2 flush is needed between steps. One step = one sk_apply (zero Y, the tile kernel, and the
 chunk-finish kernel when chunks are split into slices).
 
@@ -314,7 +314,7 @@ def main() -> int:
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--rule", default="fp16_rn", choices=["fp32", "fp16_rn", "fp16_sr", "fp16_dither"])
+    ap.add_argument("--rule", default="fp16_rn", choices=["fp32", "fp16_rn", "fp16_sr", "fp16_dither", "bf16_rn"])
     ap.add_argument("--no-extras", action="store_true", help="skip variants, distortion, cpu baseline, serving")
     ap.add_argument("--extras", default="serve",
                     help="comma list of extra measurements: serve (default), solve, batch, all")
@@ -432,16 +432,18 @@ def main() -> int:
             es2 = 4 if rv == 0 else 2
             variants[name] = {"GB/s": (m * n * 4 + d * n * es2) / (statistics.mean(per) * 1e-3) / 1e9,
                               "ms": statistics.mean(per)}
-            if name in ("fp32", "fp16_rn"):
-                etas[name] = Yv.double().cpu().numpy()
+            etas[name] = Yv.double().cpu().numpy()
             p2.close()
-        # Distortion eta(S, Q) of the column space of A (A = Q R_A), FP16 vs FP32 (same S).
+        # Distortion eta(S, Q) of the column space of A (A = Q R_A) for every rule (same S).
         import oracle
         R_A = oracle.tall_r_factor(A_h)
         eta = {nm: oracle.distortion_of(Yv, R_A) for nm, Yv in etas.items()}
         extras["variants"] = variants
         extras["distortion"] = {"eta_fp32": eta["fp32"], "eta_fp16_rn": eta["fp16_rn"],
                                 "rel_diff": abs(eta["fp16_rn"] - eta["fp32"]) / eta["fp32"],
+                                "eta_fp16_sr": eta["fp16_sr"], "eta_fp16_dither": eta["fp16_dither"],
+                                "eta_bf16_rn": eta["bf16_rn"],
+                                "rel_diff_bf16": abs(eta["bf16_rn"] - eta["fp32"]) / eta["fp32"],
                                 "gaussian_reference_sqrt_n_over_d": float(np.sqrt(n / d))}
         extras["fp16_vs_fp32_speedup"] = variants["fp16_rn"]["GB/s"] / variants["fp32"]["GB/s"]
         gb, cores, sample = cpu_oracle_rate(m, n, d, k, budget_s=10.0)
