@@ -169,6 +169,25 @@ SK_API sk_status sk_solve(sk_plan plan, const float* A_dev, int64_t lda, int64_t
 SK_API sk_status sk_solve_status(sk_plan plan, double* kappa, void* stream);
 
 /*
+ * sk_solve_precond — sketch-and-precondition least squares: x = argmin ||A x - b||_2 in FP64.
+ * The sketch S [A | b] and its FP64 QR are formed exactly as by sk_solve (same plan, rule and
+ * chunking); R then serves as a right preconditioner for LSQR (Paige and Saunders, 1982) on A itself,
+ * started from the sketch-and-solve solution. The paper's discussion names this use of the sketch
+ * (R of S A as a preconditioner) beside sketch-and-solve (Sec. 5.1). Since A R^{-1} has singular
+ * values within the sketch's distortion of 1, a few tens of iterations reach the least-squares
+ * solution of A, whatever the rounding rule of the sketch.
+ *   A_dev, lda, n, b_dev: as for sk_solve (n <= 512). x_dev: n doubles on the device (output).
+ *   max_iters: iteration limit (<= 0: 100). tol: stop when the estimate of
+ *     ||(A R^{-1})^T r|| / (||A R^{-1}||_F ||r||) <= tol or ||r|| <= tol ||b - A x0|| (<= 0: 1e-10).
+ *   iters_out (may be NULL): iterations used.
+ * Every iteration runs on the GPU in FP64; the call synchronizes `stream` every few iterations to
+ * test convergence and returns when x_dev is written. Scratch (m + 9n doubles) is plan-owned.
+ * Errors: as sk_solve; SK_ERR_NUMERIC if S A is rank deficient (no preconditioner).
+ */
+SK_API sk_status sk_solve_precond(sk_plan plan, const float* A_dev, int64_t lda, int64_t n, const float* b_dev,
+                                  double* x_dev, int32_t max_iters, double tol, int32_t* iters_out, void* stream);
+
+/*
  * sk_materialize_S — write the nonzero pattern of S for rows [i0, i0+cnt) on the device:
  * rows_dev[(i-i0)*k + j] = target row of block j (int32), signs_dev[...] = +1 or -1 (int8).
  * The same generator the sketch kernels use; for verification of the pattern.

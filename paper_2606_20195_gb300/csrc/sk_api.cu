@@ -55,6 +55,8 @@ struct sk_plan_s {
   size_t det_P_bytes = 0;
   unsigned* dstatus = nullptr;  // sticky device status word of the sketch kernels
   float* tileP = nullptr;       // two-level chunk totals (zero between launches)
+  double* lsqr = nullptr;       // sk_solve_precond: u (m), 8 n-vectors, scalars, x0 (n floats)
+  size_t lsqr_bytes = 0;
   size_t tileP_bytes = 0;
   void* solve_buf = nullptr;
   size_t solve_bytes = 0;
@@ -770,6 +772,86 @@ sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const floa
   return SK_OK;
 }
 
+sk_status sk_solve_precond(sk_plan p, const float* A, int64_t lda, int64_t n, const float* b, double* x,
+                           int32_t max_iters, double tol, int32_t* iters_out, void* stream) {
+  clear_error();
+  if (!p) return set_error(SK_ERR_INVALID_ARG, "plan is NULL");
+  if (!x) return set_error(SK_ERR_INVALID_ARG, "x is NULL");
+  if (n > kLsqrMaxN) return set_error(SK_ERR_UNSUPPORTED, "sketch-and-precondition supports n <= %d", kLsqrMaxN);
+  if (max_iters <= 0) max_iters = 100;
+  if (!(tol > 0.0)) tol = 1e-10;
+  cudaStream_t st = (cudaStream_t)stream;
+  // Scratch: u (m doubles), v w y p z x0 (6 n-vectors), scalars, the FP32 sketch-and-solve x0.
+  const int64_t m = p->m;
+  const size_t nv = (size_t)((n + 31) / 32 * 32);
+  const size_t need = sizeof(double) * ((size_t)m + 6 * nv + kLsqrScalars) + sizeof(float) * nv;
+  if (p->lsqr_bytes < need) {
+    if (p->lsqr) cudaFree(p->lsqr);
+    p->lsqr = nullptr;
+    p->lsqr_bytes = 0;
+    if (cudaMalloc(&p->lsqr, need) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(SK_ERR_OOM, "sketch-and-precondition scratch (%zu bytes)", need);
+    }
+    p->lsqr_bytes = need;
+  }
+  double* base = p->lsqr;
+  float* x0f = reinterpret_cast<float*>(base + m + 6 * nv + kLsqrScalars);
+  sk_status s = sk_solve(p, A, lda, n, b, x0f, stream);
+  if (s != SK_OK) return s;
+  const int64_t solve_launches = p->last_launches;
+  s = sk_solve_status(p, nullptr, stream);
+  if (s != SK_OK) return s;
+  DevInfo di;
+  s = dev_info(&di);
+  if (s != SK_OK) return s;
+  LsqrLaunch L;
+  L.A = A;
+  L.lda = lda;
+  L.m = m;
+  L.n = n;
+  const SolveLayout Lo = solve_layout(p->d, n, p->rule);
+  L.R = reinterpret_cast<const double*>((char*)p->solve_buf + Lo.R);
+  L.ldr = n + 1;
+  L.u = base;
+  L.v = base + m;
+  L.w = L.v + nv;
+  L.y = L.w + nv;
+  L.p = L.y + nv;
+  L.z = L.p + nv;
+  L.x0 = L.z + nv;
+  L.sc = L.x0 + nv;
+  L.x = x;
+  int32_t launches = (int32_t)solve_launches;
+  cudaError_t e = lsqr_start(L, b, x0f, di.sms, st, &launches);
+  if (e != cudaSuccess) return cuda_fail(e, "LSQR start");
+  double sc[kLsqrScalars];
+  int32_t it = 0;
+  while (it < max_iters) {
+    e = lsqr_iterate(L, di.sms, st, &launches);
+    if (e != cudaSuccess) return cuda_fail(e, "LSQR iteration");
+    ++it;
+    if (it % 4 != 0 && it != max_iters) continue;
+    e = cudaMemcpyAsync(sc, L.sc, sizeof(sc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "LSQR convergence test");
+    if (sc[kLsqrDone] != 0.0) break;
+    const double anorm = sqrt(sc[kLsqrAnorm2]);
+    const double rnorm = sc[kLsqrRnorm], arnorm = sc[kLsqrArnorm];
+    if (!std::isfinite(rnorm) || !std::isfinite(arnorm))
+      return set_error(SK_ERR_NUMERIC, "LSQR produced a non-finite residual estimate");
+    if (rnorm <= tol * sc[kLsqrBnorm] || arnorm <= tol * anorm * rnorm) break;
+  }
+  e = lsqr_finish(L, st, &launches);
+  if (e != cudaSuccess) return cuda_fail(e, "LSQR finish");
+  e = cudaMemcpyAsync(sc, L.sc, sizeof(sc), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "LSQR result");
+  if (iters_out) *iters_out = (int32_t)sc[kLsqrIters];
+  p->last_launches = launches;
+  return SK_OK;
+}
+
 sk_status sk_solve_status(sk_plan p, double* kappa, void* stream) {
   clear_error();
   if (!p) return set_error(SK_ERR_INVALID_ARG, "plan is NULL");
@@ -795,6 +877,7 @@ void sk_destroy(sk_plan p) {
   if (p->det_P) cudaFree(p->det_P);
   if (p->dstatus) cudaFree(p->dstatus);
   if (p->tileP) cudaFree(p->tileP);
+  if (p->lsqr) cudaFree(p->lsqr);
   if (p->solve_buf) cudaFree(p->solve_buf);
   for (int b = 0; b < 2; ++b) {
     if (p->stage[b]) cudaFree(p->stage[b]);

@@ -103,6 +103,39 @@ struct SolveLaunch {
 int32_t solve_ctas(int64_t d, int64_t n, int32_t sms, size_t smem_optin);
 cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launches);
 
+// Sketch-and-precondition LSQR (sk_lsqr.cu). Device scalars (FP64) of the recurrence:
+constexpr int kLsqrMaxN = 512;
+enum : int {
+  kLsqrBeta2 = 0,   // ||u||^2 accumulated by the matvec
+  kLsqrC = 1,       // -alpha / beta, the scale of the stored u in the next matvec
+  kLsqrPhibar = 2,
+  kLsqrRhobar = 3,
+  kLsqrAlpha = 4,
+  kLsqrAnorm2 = 5,  // estimate of ||A R^{-1}||_F^2
+  kLsqrBnorm = 6,   // ||b - A x0||
+  kLsqrRnorm = 7,   // estimate of ||b - A x||
+  kLsqrArnorm = 8,  // estimate of ||(A R^{-1})^T (b - A x)||
+  kLsqrIters = 9,
+  kLsqrDone = 10,   // 1: alpha or beta vanished (exact solution reached)
+  kLsqrScalars = 16
+};
+struct LsqrLaunch {
+  const float* A;
+  int64_t lda, m, n;
+  const double* R;  // n x n upper triangular R of the sketch's QR, row stride ldr
+  int64_t ldr;
+  double* u;        // m
+  double *v, *w, *y, *p, *z, *x0;  // n each
+  double* x;        // out: n
+  double* sc;       // kLsqrScalars
+};
+// Start (x0 from the FP32 sketch-and-solve solution; r0 = b - A x0; first step), one iteration, and
+// x = x0 + R^{-1} y.
+cudaError_t lsqr_start(const LsqrLaunch& L, const float* b, const float* x0f, int sms, cudaStream_t st,
+                       int32_t* launches);
+cudaError_t lsqr_iterate(const LsqrLaunch& L, int sms, cudaStream_t st, int32_t* launches);
+cudaError_t lsqr_finish(const LsqrLaunch& L, cudaStream_t st, int32_t* launches);
+
 // Batched persistent kernel.
 struct BatchDesc;     // device-side item descriptor (sk_batch.cu)
 struct BatchWork;     // device-side work item

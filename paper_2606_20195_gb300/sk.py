@@ -25,7 +25,7 @@ SK_KERNEL_AUTO, SK_KERNEL_TILE, SK_KERNEL_LITERAL, SK_KERNEL_OWNER, SK_KERNEL_GL
 # Every symbol include/sk.h declares.
 EXPORTS = [
     "sk_version", "sk_last_error", "sk_plan_create", "sk_plan_set", "sk_plan_get", "sk_apply",
-    "sk_apply_host", "sk_solve", "sk_solve_status", "sk_materialize_S", "sk_batch_create",
+    "sk_apply_host", "sk_solve", "sk_solve_status", "sk_solve_precond", "sk_materialize_S", "sk_batch_create",
     "sk_batch_set", "sk_batch_launch", "sk_batch_info", "sk_batch_destroy", "sk_destroy",
     "sk_apply_noalloc",
 ]
@@ -75,6 +75,9 @@ def load(path: str | None = None):
     L.sk_solve.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.sk_solve_status.restype = st
     L.sk_solve_status.argtypes = [vp, ctypes.POINTER(ctypes.c_double), vp]
+    L.sk_solve_precond.restype = st
+    L.sk_solve_precond.argtypes = [vp, vp, i64, i64, vp, vp, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_int32), vp]
     L.sk_materialize_S.restype = st
     L.sk_materialize_S.argtypes = [vp, i64, i64, vp, vp, vp]
     L.sk_batch_create.restype = st
@@ -158,6 +161,15 @@ def sk_solve_status(plan: int, stream=None) -> tuple[int, float]:
     kap = ctypes.c_double()
     s = load().sk_solve_status(plan, ctypes.byref(kap), _stream_handle(stream))
     return s, kap.value
+
+
+def sk_solve_precond(plan: int, A, lda: int, n: int, b, x, max_iters: int = 0, tol: float = 0.0,
+                     stream=None) -> int:
+    """Sketch-and-precondition least squares into x (n doubles); returns the iterations used."""
+    it = ctypes.c_int32(0)
+    check(load().sk_solve_precond(plan, _ptr(A), lda, n, _ptr(b), _ptr(x), int(max_iters), float(tol),
+                                  ctypes.byref(it), _stream_handle(stream)))
+    return it.value
 
 
 def sk_materialize_S(plan: int, i0: int, cnt: int, rows, signs, stream=None) -> None:
@@ -253,6 +265,15 @@ class Plan:
             x = torch.empty(n, dtype=torch.float32, device=A.device)
         sk_solve(self.handle, A, A.stride(0), n, b, x, stream)
         return x
+
+    def solve_precond(self, A, b, x=None, max_iters: int = 0, tol: float = 0.0, stream=None):
+        """(x as float64, iterations) of the sketch-and-precondition least-squares solve."""
+        import torch
+        n = A.shape[1]
+        if x is None:
+            x = torch.empty(n, dtype=torch.float64, device=A.device)
+        it = sk_solve_precond(self.handle, A, A.stride(0), n, b, x, max_iters, tol, stream)
+        return x, it
 
     def solve_status(self, stream=None):
         return sk_solve_status(self.handle, stream)
