@@ -197,8 +197,9 @@ def run_reference(args, world, rank):
     return 0
 
 
-def bench_solve(dev, rules=(0, 1, 2, 3), m=1 << 24, n=128, d=2048, k=8, reps=3):
-    """Sketch-and-solve at the coherent least-squares shape: phase times and residual ratios."""
+def bench_solve(dev, rules=(0, 1, 2, 3, 4), m=1 << 24, n=128, d=2048, k=8, reps=3):
+    """Sketch-and-solve and sketch-and-precondition (LSQR with the sketch's R) at the coherent
+    least-squares shape: phase times, iterations and residual ratios."""
     import torch
     from paper_2606_20195_gb300 import inputs, sk
     A = inputs.device_matrix(m, n, "coherent", seed=3, device=str(dev))
@@ -213,7 +214,7 @@ def bench_solve(dev, rules=(0, 1, 2, 3), m=1 << 24, n=128, d=2048, k=8, reps=3):
     for rule in rules:
         plan = sk.Plan(d, m, k, rule, seed=11)
         x = torch.empty(n, dtype=torch.float32, device=dev)
-        Y = torch.empty((d, n), dtype=torch.float32 if rule == 0 else torch.float16, device=dev)
+        Y = torch.empty((d, n), dtype=plan.out_dtype(), device=dev)
         for _ in range(2):
             plan.solve(A, b, x)
         torch.cuda.synchronize()
@@ -230,10 +231,20 @@ def bench_solve(dev, rules=(0, 1, 2, 3), m=1 << 24, n=128, d=2048, k=8, reps=3):
             tk.append(ev[1].elapsed_time(ev[2]))
         status, kappa = plan.solve_status()
         res = float(torch.linalg.vector_norm(A.double() @ x.double() - b.double()))
+        # sketch-and-precondition on the same plan (one warm run, then timed)
+        xp, its = plan.solve_precond(A, b, tol=1e-12)
+        torch.cuda.synchronize()
+        ev[0].record()
+        xp, its = plan.solve_precond(A, b, tol=1e-12)
+        ev[1].record()
+        torch.cuda.synchronize()
+        res_p = float(torch.linalg.vector_norm(A.double() @ xp - b.double()))
         out[list(sk.RULES)[rule]] = {"solve_ms": statistics.median(ts), "sketch_A_ms": statistics.median(tk),
                                      "qr_and_Sb_ms": statistics.median(ts) - statistics.median(tk),
                                      "residual_ratio": res / r_opt, "kappa_SA_diag_estimate": kappa,
-                                     "status": status}
+                                     "status": status,
+                                     "precond": {"ms": ev[0].elapsed_time(ev[1]), "iterations": its,
+                                                 "residual_ratio": res_p / r_opt}}
         plan.close()
     del A, b
     torch.cuda.empty_cache()

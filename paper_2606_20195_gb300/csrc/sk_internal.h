@@ -124,7 +124,7 @@ struct LsqrLaunch {
   int64_t lda, m, n;
   const double* R;  // n x n upper triangular R of the sketch's QR, row stride ldr
   int64_t ldr;
-  double* u;        // m
+  double* u;        // storage of m doubles: u as (hi, lo) float pairs, first m hi then m lo
   double *v, *w, *y, *p, *z, *x0;  // n each
   double* x;        // out: n
   double* sc;       // kLsqrScalars

@@ -5,7 +5,9 @@
 // sketch's distortion of 1, so LSQR needs few iterations, and it converges to the least-squares
 // solution of A itself: the rounding rule of the sketch only changes the preconditioner.
 //
-// Everything of an iteration runs on the GPU, in FP64 (A's FP32 entries are exact in FP64):
+// Everything of an iteration runs on the GPU. The two products with A run on the FP32 pipe with
+// about twice FP32 precision (exact products and compensated sums, df_acc); vector lengths, the
+// step and the recurrence are FP64:
 //   lsqr_av_kernel    u <- A p - c u and ||u||^2           (one lane per row of A)
 //   lsqr_atu_kernel   z <- A^T u                           (warps over row runs, FP64 atomics)
 //   lsqr_step_kernel  the n-vector part: v = R^{-T} z / beta - beta v, alpha, the plane rotation,
@@ -45,49 +47,77 @@ __device__ void block_atomic_sum(double v, double* out) {
   __syncthreads();
 }
 
+// Products of A's FP32 entries with an FP64 vector y = yh + yl (two floats) accumulated in about
+// twice FP32 precision on the FP32 pipe: the product a * yh is split exactly into p + e (FMA), the
+// running sum takes p through TwoSum (Knuth), and the error terms e + a * yl and the TwoSum errors are
+// summed in a second float (cascaded summation, Ogita, Rump and Oishi, SIAM J. Sci. Comput. 2005).
+// Explicit round-to-nearest intrinsics keep the compiler from fusing the error-free steps.
+__device__ __forceinline__ void df_acc(float a, float yh, float yl, float& s, float& c) {
+  const float p = __fmul_rn(a, yh);
+  const float e = __fmaf_rn(a, yh, -p);
+  const float t = __fadd_rn(s, p);
+  const float bb = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(a, yl, e)));
+}
+
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+
 // u_i <- A_i . p + c u_i with c = sc[kLsqrC] (or b_i - A_i . p when `b` is given),
-// sc[kLsqrBeta2] += sum of u_i^2. One lane per row (no cross-lane reductions: every FP64 operation
-// is a product term), 16-byte loads when the rows allow them; p in shared memory (a broadcast).
+// sc[kLsqrBeta2] += sum of u_i^2. One lane per row; p in shared memory as (hi, lo) floats; u is
+// kept as (hi, lo) floats (uh = first m, ul = next m floats of the u buffer).
 __global__ void __launch_bounds__(256) lsqr_av_kernel(const LsqrLaunch L, const float* b) {
-  extern __shared__ double ps[];
-  const double c = b ? 0.0 : L.sc[kLsqrC];
-  for (int64_t j = threadIdx.x; j < L.n; j += blockDim.x) ps[j] = L.p[j];
-  __syncthreads();
+  extern __shared__ float pf[];  // [0, n): hi, [n, 2n): lo
   const int64_t n = L.n;
+  const double c = b ? 0.0 : L.sc[kLsqrC];
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) split_df(L.p[j], pf[j], pf[n + j]);
+  __syncthreads();
+  float* uh = reinterpret_cast<float*>(L.u);
+  float* ul = uh + L.m;
   const bool vec = (n & 3) == 0 && (L.lda & 3) == 0 && (reinterpret_cast<uintptr_t>(L.A) & 15u) == 0;
   double sq = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.m; i += (int64_t)gridDim.x * blockDim.x) {
     const float* a = L.A + i * L.lda;
-    double acc0 = 0.0, acc1 = 0.0;
+    float s = 0.f, cc = 0.f;
     if (vec) {
       for (int64_t j = 0; j < n; j += 4) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(a + j));
-        acc0 = fma((double)v.x, ps[j], acc0);
-        acc1 = fma((double)v.y, ps[j + 1], acc1);
-        acc0 = fma((double)v.z, ps[j + 2], acc0);
-        acc1 = fma((double)v.w, ps[j + 3], acc1);
+        df_acc(v.x, pf[j], pf[n + j], s, cc);
+        df_acc(v.y, pf[j + 1], pf[n + j + 1], s, cc);
+        df_acc(v.z, pf[j + 2], pf[n + j + 2], s, cc);
+        df_acc(v.w, pf[j + 3], pf[n + j + 3], s, cc);
       }
     } else {
-      for (int64_t j = 0; j < n; ++j) acc0 = fma((double)__ldg(a + j), ps[j], acc0);
+      for (int64_t j = 0; j < n; ++j) df_acc(__ldg(a + j), pf[j], pf[n + j], s, cc);
     }
-    const double s = acc0 + acc1;
-    const double u = b ? ((double)b[i] - s) : fma(c, L.u[i], s);
-    L.u[i] = u;
+    const double dot = (double)s + (double)cc;
+    const double u = b ? ((double)b[i] - dot) : fma(c, (double)uh[i] + (double)ul[i], dot);
+    float h, l;
+    split_df(u, h, l);
+    uh[i] = h;
+    ul[i] = l;
     sq = fma(u, u, sq);
   }
   block_atomic_sum(sq, L.sc + kLsqrBeta2);
 }
 
 // z <- z + A^T u over this CTA's rows (z zero before the launch). Each warp takes a contiguous run of
-// rows; lane l keeps the partial sums of columns l, l + 32, ... (NPL of them, NPL * 32 >= n), 4 rows
-// per step; the CTA's warps then combine their sums in shared memory and add them with FP64 atomics.
+// rows; lane l keeps the partial sums of columns l, l + 32, ... (NPL of them, NPL * 32 >= n) as
+// (s, c) float pairs, 4 rows per step; the CTA's warps combine their sums in FP64 in shared memory and
+// add them with FP64 atomics.
 template <int NPL>
 __global__ void __launch_bounds__(256) lsqr_atu_kernel(const LsqrLaunch L) {
   __shared__ double zs[8][NPL * 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double acc[NPL];
+  float sh[NPL], cl[NPL];
 #pragma unroll
-  for (int q = 0; q < NPL; ++q) acc[q] = 0.0;
+  for (int q = 0; q < NPL; ++q) sh[q] = cl[q] = 0.f;
+  const float* uh = reinterpret_cast<const float*>(L.u);
+  const float* ul = uh + L.m;
   const int64_t nwt = (int64_t)gridDim.x * 8;
   const int64_t wg = (int64_t)blockIdx.x * 8 + warp;
   const int64_t rows_per = (L.m + nwt - 1) / nwt;
@@ -95,32 +125,36 @@ __global__ void __launch_bounds__(256) lsqr_atu_kernel(const LsqrLaunch L) {
   const int64_t r1 = min(L.m, r0 + rows_per);
   int64_t i = r0;
   for (; i + 4 <= r1; i += 4) {
-    const double u0 = L.u[i], u1 = L.u[i + 1], u2 = L.u[i + 2], u3 = L.u[i + 3];
+    float h[4], l[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      h[t] = uh[i + t];
+      l[t] = ul[i + t];
+    }
     const float* a = L.A + i * L.lda;
 #pragma unroll
     for (int q = 0; q < NPL; ++q) {
       const int64_t j = lane + 32 * q;
       if (j < L.n) {
-        double t = acc[q];
-        t = fma((double)__ldg(a + j), u0, t);
-        t = fma((double)__ldg(a + L.lda + j), u1, t);
-        t = fma((double)__ldg(a + 2 * L.lda + j), u2, t);
-        t = fma((double)__ldg(a + 3 * L.lda + j), u3, t);
-        acc[q] = t;
+        float av[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) av[t] = __ldg(a + t * L.lda + j);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) df_acc(av[t], h[t], l[t], sh[q], cl[q]);
       }
     }
   }
   for (; i < r1; ++i) {
-    const double u = L.u[i];
+    const float h = uh[i], l = ul[i];
     const float* a = L.A + i * L.lda;
 #pragma unroll
     for (int q = 0; q < NPL; ++q) {
       const int64_t j = lane + 32 * q;
-      if (j < L.n) acc[q] = fma((double)__ldg(a + j), u, acc[q]);
+      if (j < L.n) df_acc(__ldg(a + j), h, l, sh[q], cl[q]);
     }
   }
 #pragma unroll
-  for (int q = 0; q < NPL; ++q) zs[warp][lane + 32 * q] = acc[q];
+  for (int q = 0; q < NPL; ++q) zs[warp][lane + 32 * q] = (double)sh[q] + (double)cl[q];
   __syncthreads();
   for (int64_t j = threadIdx.x; j < L.n; j += blockDim.x) {
     double t = 0.0;
@@ -274,7 +308,7 @@ cudaError_t lsqr_start(const LsqrLaunch& L, const float* b, const float* x0f, in
                        int32_t* launches) {
   lsqr_start_kernel<<<1, 512, 0, st>>>(L, x0f);
   // u = b - A x0, ||u||^2
-  lsqr_av_kernel<<<(unsigned)av_grid(L.m, sms), 256, L.n * sizeof(double), st>>>(L, b);
+  lsqr_av_kernel<<<(unsigned)av_grid(L.m, sms), 256, 2 * L.n * sizeof(float), st>>>(L, b);
   launch_atu(L, sms, st);
   lsqr_step_kernel<<<1, 512, 0, st>>>(L, 1);
   if (launches) *launches += 4;
@@ -283,7 +317,7 @@ cudaError_t lsqr_start(const LsqrLaunch& L, const float* b, const float* x0f, in
 
 cudaError_t lsqr_iterate(const LsqrLaunch& L, int sms, cudaStream_t st, int32_t* launches) {
   // u <- A p + c u with c = -alpha / beta, written by the previous step kernel
-  lsqr_av_kernel<<<(unsigned)av_grid(L.m, sms), 256, L.n * sizeof(double), st>>>(L, nullptr);
+  lsqr_av_kernel<<<(unsigned)av_grid(L.m, sms), 256, 2 * L.n * sizeof(float), st>>>(L, nullptr);
   launch_atu(L, sms, st);
   lsqr_step_kernel<<<1, 512, 0, st>>>(L, 0);
   if (launches) *launches += 3;
