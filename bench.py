@@ -46,6 +46,12 @@ KERNEL_SOURCES = ["paper_2606_20195_gb300/csrc/sk_tile.cuh", "paper_2606_20195_g
                   "paper_2606_20195_gb300/csrc/sk_device.cuh"]
 
 
+def y_dtype(rule: int):
+    """torch dtype of Y for a rule: float32, binary16, or bfloat16 (rule 4)."""
+    import torch
+    return torch.float32 if rule == 0 else (torch.bfloat16 if rule == 4 else torch.float16)
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
@@ -260,7 +266,7 @@ def bench_batch(dev, rule_name="fp16_rn", count=256, reps=5):
     total = 0
     for i, (m, n, fam) in enumerate(inputs.batch_shapes(count, seed=0)):
         A = inputs.device_matrix(m, n, fam, seed=100 + i, device=str(dev))
-        Y = torch.empty((32 * n, n), dtype=torch.float32 if rule == 0 else torch.float16, device=dev)
+        Y = torch.empty((32 * n, n), dtype=y_dtype(rule), device=dev)
         items.append({"A": A, "Y": Y, "m": m, "n": n, "d": 32 * n, "k": 4, "seed": i})
         total += m * n * 4 + 32 * n * n * (4 if rule == 0 else 2)
     b, params = autotune.tune_batch(items, rule, reps=2)
@@ -355,11 +361,11 @@ def main() -> int:
     A_h = inputs.host_matrix(m, n, "incoherent", seed=rank)
     A_pin = torch.from_numpy(A_h).pin_memory()
     A = A_pin.to(dev)
-    Yb = torch.empty((d, n), dtype=torch.float32 if rule == 0 else torch.float16, device=dev)
+    Yb = torch.empty((d, n), dtype=y_dtype(rule), device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def timed(plan_h, rule_v, steps, warmup):
-        Y = torch.empty((d, n), dtype=torch.float32 if rule_v == 0 else torch.float16, device=dev)
+        Y = torch.empty((d, n), dtype=y_dtype(rule_v), device=dev)
         for _ in range(warmup):
             sk.sk_apply(plan_h, A, n, n, Y, stream)
         torch.cuda.synchronize()
@@ -394,7 +400,7 @@ def main() -> int:
     value = world * bytes_step * args.steps / (max_ms * 1e-3) / 1e9
 
     # e2e through the host-buffer entry point (pinned A in, pinned Y out)
-    Y_pin = torch.empty((d, n), dtype=torch.float32 if rule == 0 else torch.float16).pin_memory()
+    Y_pin = torch.empty((d, n), dtype=y_dtype(rule)).pin_memory()
     for _ in range(2):
         sk.sk_apply_host(plan.handle, A_pin.data_ptr(), n, n, Y_pin.data_ptr(), stream)
     e2e_steps = max(3, min(args.steps, 10))
