@@ -257,6 +257,97 @@ def bench_solve(dev, rules=(0, 1, 2, 3, 4), m=1 << 24, n=128, d=2048, k=8, reps=
     return {"workload": f"coherent LS m={m} n={n} d={d} k={k}", **out}
 
 
+def eta_of(SU) -> float:
+    """Distortion eta(S, U) = max(|sigma_max(SU) - 1|, |1 - sigma_min(SU)|) of a sketched orthonormal
+    basis (paper Sec. 5.1), from the eigenvalues of the n x n Gram matrix (SU)^T (SU) in FP64."""
+    import torch
+    X = SU.double()
+    ev = torch.linalg.eigvalsh(X.T @ X).clamp_min(0.0).sqrt()
+    return float(max(abs(float(ev[-1]) - 1.0), abs(1.0 - float(ev[0]))))
+
+
+def coherence_of(U) -> float:
+    """mu(U) = (m/n) max_i ||U_i,:||^2 (paper Sec. 5.2, coherence sweep)."""
+    m, n = U.shape
+    return float((U.double() ** 2).sum(dim=1).max()) * m / n
+
+
+def bench_paper(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 32, 64, 128, 256),
+                sweep_ratios=(2, 4, 8, 16), alphas=(0.0, 0.3, 0.6, 0.8, 0.9, 0.95, 1.0), reps=3):
+    """The paper's sketching experiments on synthetic inputs (Sec. 5.1-5.2): distortion eta and
+    throughput over the sketch ratio d/n for a Gaussian and an identity-like orthonormal basis
+    U (m x n), and the coherence sweep U(alpha) = orth((1 - alpha) Q_rand + alpha [I; 0]).
+    SparseStack (k = 8) with every rounding rule and CountSketch (k = 1); U itself is the sketched
+    matrix (its GB/s is the throughput). Inputs are built with torch (FP32 QR), not by the library."""
+    import torch
+    from paper_2606_20195_gb300 import sk
+    torch.backends.cuda.matmul.allow_tf32 = False
+    g = torch.Generator(device=dev)
+    g.manual_seed(2606)
+    methods = [("sparsestack", 8, r) for r in ("fp32", "fp16_rn", "fp16_sr", "fp16_dither", "bf16_rn")]
+    methods += [("countsketch", 1, "fp32"), ("countsketch", 1, "fp16_rn")]
+
+    def sketch(U, d, k, rule_name, timed=False):
+        rv = sk.RULES[rule_name]
+        plan = sk.Plan(d, U.shape[0], k, rv, seed=77)
+        Y = torch.empty((d, U.shape[1]), dtype=y_dtype(rv), device=dev)
+        ms = None
+        if timed:
+            for _ in range(2):
+                plan.apply(U, Y)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                plan.apply(U, Y)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+        else:
+            plan.apply(U, Y)
+        plan.close()
+        return Y.float(), ms
+
+    out = {"workload": f"n={n} m={m}, d/n in {list(ratios)}; SparseStack k=8, CountSketch k=1", "extremes": {}}
+    Qg = torch.linalg.qr(torch.randn((m, n), generator=g, device=dev)).Q.contiguous()
+    Qc = torch.zeros((m, n), device=dev)
+    Qc[:n] = torch.eye(n, device=dev)
+    for fam, U in (("gaussian", Qg), ("identity", Qc)):
+        res = {}
+        for name, k, rname in methods:
+            key = f"{name}_{rname}"
+            etas, gbs = [], []
+            for r in ratios:
+                d = r * n
+                Y, ms = sketch(U, d, k, rname, timed=(fam == "gaussian"))
+                etas.append(eta_of(Y))
+                es = 4 if rname == "fp32" else 2
+                gbs.append((m * n * 4 + d * n * es) / (ms * 1e-3) / 1e9 if ms else None)
+                del Y
+            res[key] = {"eta": etas, "GB/s": gbs} if fam == "gaussian" else {"eta": etas}
+        res["gaussian_reference_sqrt_n_over_d"] = [float(np.sqrt(1.0 / r)) for r in ratios]
+        out["extremes"][fam] = res
+    # coherence sweep
+    sweep = {"alpha": list(alphas), "mu": [], "d_over_n": list(sweep_ratios)}
+    sweep_methods = [mt for mt in methods if mt[2] in ("fp32", "fp16_rn", "fp16_sr", "fp16_dither") and
+                     (mt[0] == "sparsestack" or mt[2] == "fp32")]
+    for name, k, rname in sweep_methods:
+        sweep[f"{name}_{rname}"] = {str(r): [] for r in sweep_ratios}
+    for a in alphas:
+        U = torch.linalg.qr((1.0 - a) * Qg + a * Qc).Q.contiguous()
+        sweep["mu"].append(coherence_of(U))
+        for name, k, rname in sweep_methods:
+            for r in sweep_ratios:
+                Y, _ = sketch(U, r * n, k, rname)
+                sweep[f"{name}_{rname}"][str(r)].append(eta_of(Y))
+                del Y
+        del U
+    out["coherence_sweep"] = sweep
+    del Qg, Qc
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_batch(dev, rule_name="fp16_rn", count=256, reps=5):
     """256 uneven matrices in one persistent launch, captured in a CUDA graph and replayed."""
     import torch
@@ -467,7 +558,7 @@ def main() -> int:
         cpu_baseline = {"value": gb, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample}
         want = set(args.extras.split(",")) if args.extras else set()
         if "all" in want:
-            want = {"serve", "solve", "batch"}
+            want = {"serve", "solve", "batch"}  # "paper" (minutes) only when asked for by name
         del A_pin
         if "serve" in want:
             extras["serving"] = bench_serve(dev)
@@ -476,6 +567,8 @@ def main() -> int:
             extras["sketch_and_solve"] = bench_solve(dev)
         if "batch" in want:
             extras["batched"] = bench_batch(dev)
+        if "paper" in want:
+            extras["paper_experiments"] = bench_paper(dev)
 
     if rank == 0:
         line = {
