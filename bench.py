@@ -348,6 +348,102 @@ def bench_paper(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 32, 64, 128, 256),
     return out
 
 
+def bench_paper_ls(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 24), reps=2):
+    """The paper's sketch-and-solve least-squares families (Sec. 5.3) on synthetic inputs: dense
+    A = U Sigma V^T (singular values 100 -> 1, b = A 1 + noise; "easy": noise 1e-3 N(0,1), "hard":
+    noise 1e-1 N(0,1) plus an offset of 1e-1) and the coherent permuted [I_n; tau G / sqrt(m-n)]
+    (tau = 1e-3, noise 0.5 on the identity block). Per sketch ratio and method: sk_solve time,
+    relative residual ||Ax - b|| / ||b|| and kappa(SA) (FP64 Gram eigenvalues of the sketch).
+    The least-squares optimum (FP64 QR of [A | b] by torch) is the normal-equations reference.
+    On the coherent problem the paper's per-element FP16 scheme (R = 1, literal kernel) also runs."""
+    import torch
+    from paper_2606_20195_gb300 import sk
+    torch.backends.cuda.matmul.allow_tf32 = False
+    g = torch.Generator(device=dev)
+    g.manual_seed(5303)
+    methods = [("sparsestack", 8, r) for r in ("fp32", "fp16_rn", "fp16_sr", "fp16_dither", "bf16_rn")]
+    methods += [("countsketch", 1, "fp32"), ("countsketch", 1, "fp16_rn")]
+    step = 1 << 18
+
+    def rel_res(A, b, x):
+        x64 = x.double()
+        acc = 0.0
+        for i0 in range(0, A.shape[0], step):
+            r = A[i0:i0 + step].double() @ x64 - b[i0:i0 + step].double()
+            acc += float(r @ r)
+        return (acc ** 0.5) / float(torch.linalg.vector_norm(b.double()))
+
+    def optimum(A, b):
+        Rs = []
+        for i0 in range(0, A.shape[0], step):
+            blk = torch.cat([A[i0:i0 + step].double(), b[i0:i0 + step].double()[:, None]], dim=1)
+            Rs.append(torch.linalg.qr(blk, mode="r").R)
+        R = torch.linalg.qr(torch.cat(Rs), mode="r").R
+        return float(abs(R[n, n])) / float(torch.linalg.vector_norm(b.double()))
+
+    def problems():
+        U = torch.linalg.qr(torch.randn((m, n), generator=g, device=dev)).Q
+        V = torch.linalg.qr(torch.randn((n, n), generator=g, device=dev)).Q
+        sig = torch.linspace(100.0, 1.0, n, device=dev)
+        A = ((U * sig) @ V.T).contiguous()
+        del U
+        Ae = A.sum(dim=1)
+        yield "dense_easy", A, (Ae + 1e-3 * torch.randn(m, generator=g, device=dev)).contiguous()
+        yield "dense_hard", A, (Ae + 1e-1 * torch.randn(m, generator=g, device=dev) + 1e-1).contiguous()
+        del A, Ae
+        tau = 1e-3
+        G = torch.randn((m - n, n), generator=g, device=dev) * (tau / (m - n) ** 0.5)
+        xs = torch.randn(n, generator=g, device=dev)
+        A = torch.cat([torch.eye(n, device=dev), G])
+        b = torch.cat([xs + 0.5 * torch.randn(n, generator=g, device=dev), G @ xs])
+        del G
+        perm = torch.randperm(m, generator=g, device=dev)
+        yield "coherent_permuted", A[perm].contiguous(), b[perm].contiguous()
+
+    out = {"workload": f"m={m} n={n}, d/n in {list(ratios)}; SparseStack k=8, CountSketch k=1", "families": {}}
+    for name, A, b in problems():
+        fam = {"optimum_rel_res": optimum(A, b)}
+        for r in ratios:
+            d = r * n
+            row = {}
+            # the paper's per-element scheme (R = 1, one FP16 atomic per contribution) beside the
+            # chunked one, on the coherent problem at the two smallest ratios
+            extra = [("sparsestack_literal", 8, "fp16_rn")] if name.startswith("coherent") and r <= 4 else []
+            for meth, k, rname in methods + extra:
+                params = {"kernel": sk.SK_KERNEL_LITERAL, "chunk_rows": 1} if meth.endswith("literal") else {}
+                plan = sk.Plan(d, m, k, sk.RULES[rname], seed=31, **params)
+                x = plan.solve(A, b)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ts = []
+                for _ in range(reps):
+                    e0.record()
+                    plan.solve(A, b, x)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                status, kd = plan.solve_status()
+                launches = plan.get(sk.SK_PARAM_LAST_LAUNCHES)
+                Y = torch.empty((d, n), dtype=y_dtype(sk.RULES[rname]), device=dev)
+                e0.record()
+                plan.apply(A, Y)
+                e1.record()
+                torch.cuda.synchronize()
+                X = Y.double()
+                ev = torch.linalg.eigvalsh(X.T @ X).clamp_min(0.0)
+                kap = float((ev[-1] / ev[0]) ** 0.5) if float(ev[0]) > 0 else float("inf")
+                row[f"{meth}_{rname}"] = {"ms": statistics.median(ts), "sketch_A_ms": e0.elapsed_time(e1),
+                                          "rel_res": rel_res(A, b, x), "kappa_SA": kap, "kappa_diag_estimate": kd,
+                                          "status": status, "solve_launches": launches}
+                del Y, X
+                plan.close()
+            fam[str(r)] = row
+        out["families"][name] = fam
+        del A, b
+        torch.cuda.empty_cache()
+    return out
+
+
 def bench_batch(dev, rule_name="fp16_rn", count=256, reps=5):
     """256 uneven matrices in one persistent launch, captured in a CUDA graph and replayed."""
     import torch
@@ -569,6 +665,7 @@ def main() -> int:
             extras["batched"] = bench_batch(dev)
         if "paper" in want:
             extras["paper_experiments"] = bench_paper(dev)
+            extras["paper_least_squares"] = bench_paper_ls(dev)
 
     if rank == 0:
         line = {

@@ -98,7 +98,10 @@ typedef enum {
   /* Read-only: the kernel the last sketch ran: SK_KERNEL_TILE (1), SK_KERNEL_LITERAL (2),
    * SK_KERNEL_OWNER (3), SK_KERNEL_GLOBAL (4), or 5 for the deterministic-mode kernel; 0 before the
    * first sketch. */
-  SK_PARAM_LAST_KERNEL = 10
+  SK_PARAM_LAST_KERNEL = 10,
+  /* Rows per group of sk_solve's tree QR (0, the default: as many rows as the GPU's shared memory
+   * holds, so a sketch that fits is factored by one launch). Values below 2n are raised to 2n. */
+  SK_PARAM_SOLVE_GROUP_ROWS = 11
 } sk_param;
 
 enum { SK_MODE_ATOMIC = 0, SK_MODE_DETERMINISTIC = 1, SK_MODE_SERIAL_TILE = 2 };
@@ -152,8 +155,10 @@ SK_API sk_status sk_apply_host(sk_plan plan, const float* A_host, int64_t lda, i
  * sk_solve — sketch-and-solve least squares (paper Sec. 5.1): x = argmin ||(S A) x - (S b)||_2.
  * SA and Sb are formed with this plan's S and rule (Sb uses the same chunking, as column n of
  * [A | b]), converted to FP64, factored by a Householder QR on the device, and x is recovered by
- * Q^T (S b) and back substitution, all in FP64; x is written as FP32.
- *   A_dev, lda, n as in sk_apply; requires n <= d and n <= 512.
+ * Q^T (S b) and back substitution, all in FP64; x is written as FP32. A sketch taller than the
+ * GPU's shared memory holds is factored as a tree: groups of rows are factored separately and
+ * their triangular factors (with Q^T Sb) stacked and factored again (SK_PARAM_SOLVE_GROUP_ROWS).
+ *   A_dev, lda, n as in sk_apply; requires n <= d and n <= 1024.
  *   b_dev  device, m floats; x_dev device, n floats.
  * Device scratch (d x (n+1) sketch and FP64 workspace) is allocated on first use and grown as
  * needed; calls after the first with the same or smaller n allocate nothing.

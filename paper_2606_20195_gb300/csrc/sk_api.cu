@@ -48,6 +48,7 @@ struct sk_plan_s {
   int32_t kernel = SK_KERNEL_AUTO;
   int32_t tile_cols = 0;
   int32_t threads = 0;
+  int64_t solve_group_rows = 0;  // rows per QR group of sk_solve (0: as many as shared memory holds)
   int64_t last_launches = 0, last_R = 0;
   int32_t last_kernel = 0;  // kernel of the last sketch: 1 tile, 2 literal, 3 owner, 4 global, 5 deterministic
   // device scratch
@@ -75,7 +76,7 @@ namespace {
 
 constexpr int32_t kMaxK = 64;
 constexpr int64_t kMaxN = 65535;
-constexpr int32_t kMaxSolveN = 512;
+constexpr int32_t kMaxSolveN = 1024;
 
 sk_status cuda_fail(cudaError_t e, const char* what) {
   return set_error(SK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -521,6 +522,10 @@ sk_status sk_plan_set(sk_plan p, int32_t key, int64_t v) {
         return set_error(SK_ERR_INVALID_ARG, "threads must be 0 or a multiple of 32 in [128, 1024]");
       p->threads = (int32_t)v;
       return SK_OK;
+    case SK_PARAM_SOLVE_GROUP_ROWS:
+      if (v < 0) return set_error(SK_ERR_INVALID_ARG, "solve group rows must be >= 0");
+      p->solve_group_rows = v;
+      return SK_OK;
     default:
       return set_error(SK_ERR_INVALID_ARG, "unknown or read-only key %d", key);
   }
@@ -536,6 +541,7 @@ sk_status sk_plan_get(sk_plan p, int32_t key, int64_t* v) {
     case SK_PARAM_KERNEL: *v = p->kernel; return SK_OK;
     case SK_PARAM_TILE_COLS: *v = p->tile_cols; return SK_OK;
     case SK_PARAM_THREADS: *v = p->threads; return SK_OK;
+    case SK_PARAM_SOLVE_GROUP_ROWS: *v = p->solve_group_rows; return SK_OK;
     case SK_PARAM_LAST_LAUNCHES: *v = p->last_launches; return SK_OK;
     case SK_PARAM_LAST_CHUNK_ROWS: *v = p->last_R; return SK_OK;
     case SK_PARAM_LAST_KERNEL: *v = p->last_kernel; return SK_OK;
@@ -690,10 +696,11 @@ sk_status sk_materialize_S(sk_plan p, int64_t i0, int64_t cnt, int32_t* rows, in
 //   bcast (n doubles), bar (2 words), status (1 word), kappa (1 double).
 namespace {
 struct SolveLayout {
-  size_t ya, yb, part, R, bcast, bar, status, kappa, total;
+  size_t ya, yb, part, R, bcast, bar, status, kappa, stack[2], total;
 };
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
-SolveLayout solve_layout(int64_t d, int64_t n, int32_t rule) {
+// stack_groups: groups of the first tree level (0: the sketch is factored by one launch).
+SolveLayout solve_layout(int64_t d, int64_t n, int32_t rule, int64_t stack_groups) {
   SolveLayout L;
   size_t off = 0;
   const size_t es = elem_size(rule);
@@ -705,8 +712,23 @@ SolveLayout solve_layout(int64_t d, int64_t n, int32_t rule) {
   L.bar = off; off = al256(off + 8);
   L.status = off; off = al256(off + 4);
   L.kappa = off; off = al256(off + 8);
+  for (int i = 0; i < 2; ++i) {
+    L.stack[i] = off;
+    off = al256(off + 8 * (size_t)(stack_groups * n * (n + 1)));
+  }
   L.total = off;
   return L;
+}
+
+// Rows per group of the QR tree for a d x (n+1) sketch: the whole sketch if it fits one launch,
+// else a cap of at least 2n rows (each level then shrinks the stack at least by half). 0: unsupported.
+int64_t solve_group_cap(const sk_plan_s* p, int64_t n, const DevInfo& di) {
+  const int64_t cap_auto = solve_rows_cap(n, di.sms, (size_t)di.optin);
+  if (cap_auto < n) return 0;
+  int64_t cap = cap_auto;
+  if (p->solve_group_rows > 0) cap = std::min(cap, std::max(p->solve_group_rows, 2 * n));
+  if (p->d > cap && cap < 2 * n) return 0;
+  return cap;
 }
 }  // namespace
 
@@ -720,9 +742,12 @@ sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const floa
   DevInfo di;
   s = dev_info(&di);
   if (s != SK_OK) return s;
-  const int32_t ncta = solve_ctas(p->d, n, di.sms, (size_t)di.optin);
-  if (ncta < 1) return set_error(SK_ERR_UNSUPPORTED, "FP64 QR of a %lld x %lld sketch does not fit", (long long)p->d, (long long)(n + 1));
-  const SolveLayout Lo = solve_layout(p->d, n, p->rule);
+  const int64_t cap = solve_group_cap(p, n, di);
+  if (cap < 1)
+    return set_error(SK_ERR_UNSUPPORTED, "FP64 QR of a %lld x %lld sketch: too many columns for shared memory",
+                     (long long)p->d, (long long)(n + 1));
+  const int64_t groups1 = (p->d > cap) ? (p->d + cap - 1) / cap : 0;
+  const SolveLayout Lo = solve_layout(p->d, n, p->rule, groups1);
   if (p->solve_bytes < Lo.total) {
     if (p->solve_buf) cudaFree(p->solve_buf);
     p->solve_buf = nullptr;
@@ -754,17 +779,50 @@ sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const floa
   SolveLaunch L;
   L.SA = base + Lo.ya;
   L.Sb = base + Lo.yb;
+  L.lda_sa = n;
+  L.sb_stride = 1;
   L.rule = p->rule;
-  L.d = p->d;
+  L.src_fp64 = 0;
   L.n = n;
   L.part = (double*)(base + Lo.part);
-  L.R = (double*)(base + Lo.R);
   L.bcast = (double*)(base + Lo.bcast);
   L.bar = (unsigned*)(base + Lo.bar);
   L.status = (unsigned*)(base + Lo.status);
   L.kappa = (double*)(base + Lo.kappa);
   L.x = x;
-  L.ncta = ncta;
+  // Tree levels: factor groups of at most `cap` rows, stack their [R | c] factors, repeat.
+  int64_t rows = p->d;
+  int level = 0;
+  while (rows > cap) {
+    const int64_t g = (rows + cap - 1) / cap;
+    double* dst = (double*)(base + Lo.stack[level & 1]);
+    const size_t es_src = L.src_fp64 ? sizeof(double) : elem_size(p->rule);
+    for (int64_t gi = 0; gi < g; ++gi) {
+      const int64_t r0 = gi * rows / g, r1 = (gi + 1) * rows / g;
+      SolveLaunch G = L;
+      G.SA = (const char*)L.SA + es_src * (size_t)(r0 * L.lda_sa);
+      G.Sb = (const char*)L.Sb + es_src * (size_t)(r0 * L.sb_stride);
+      G.d = r1 - r0;
+      G.R = dst + gi * n * (n + 1);
+      G.solve_x = 0;
+      G.ncta = solve_ctas(G.d, n, di.sms, (size_t)di.optin);
+      if (G.ncta < 1) return set_error(SK_ERR_UNSUPPORTED, "QR group of %lld rows does not fit", (long long)G.d);
+      e = launch_solve(G, st, &launches);
+      if (e != cudaSuccess) return cuda_fail(e, "QR group launch");
+    }
+    L.SA = dst;
+    L.Sb = dst + n;
+    L.lda_sa = n + 1;
+    L.sb_stride = n + 1;
+    L.src_fp64 = 1;
+    rows = g * n;
+    ++level;
+  }
+  L.d = rows;
+  L.R = (double*)(base + Lo.R);
+  L.solve_x = 1;
+  L.ncta = solve_ctas(rows, n, di.sms, (size_t)di.optin);
+  if (L.ncta < 1) return set_error(SK_ERR_UNSUPPORTED, "FP64 QR of a %lld x %lld matrix does not fit", (long long)rows, (long long)(n + 1));
   e = launch_solve(L, st, &launches);
   if (e != cudaSuccess) return cuda_fail(e, "QR launch");
   p->last_launches = launches;
@@ -810,7 +868,7 @@ sk_status sk_solve_precond(sk_plan p, const float* A, int64_t lda, int64_t n, co
   L.lda = lda;
   L.m = m;
   L.n = n;
-  const SolveLayout Lo = solve_layout(p->d, n, p->rule);
+  const SolveLayout Lo = solve_layout(p->d, n, p->rule, 0);  // the offset of R does not depend on the tree
   L.R = reinterpret_cast<const double*>((char*)p->solve_buf + Lo.R);
   L.ldr = n + 1;
   L.u = base;

@@ -86,9 +86,12 @@ cudaError_t launch_pattern(int64_t d, int32_t k, uint64_t seed, int64_t i0, int6
 
 // FP64 sketch-and-solve back end: QR of [SA | Sb] (d x (n+1)), x = R^-1 (Q^T Sb)[:n].
 struct SolveLaunch {
-  const void* SA;   // d x n, float or binary16 (rule)
-  const void* Sb;   // d, same type
+  const void* SA;   // d x n, row stride lda_sa; float, binary16 or bfloat16 (rule), or FP64 (src_fp64)
+  const void* Sb;   // d values with stride sb_stride, same type
+  int64_t lda_sa = 0, sb_stride = 1;
   int32_t rule;
+  int32_t src_fp64 = 0;  // 1: SA and Sb are FP64 (a stack of [R | c] factors of a tree level)
+  int32_t solve_x = 1;   // 1: back substitution into x and kappa; 0: write [R | c] only (zero below the diagonal)
   int64_t d, n;
   double* part;     // scratch: partial sums, (ncta) * (n + 2) doubles
   double* R;        // scratch: n x (n+1) doubles (R and Q^T Sb)
@@ -101,6 +104,8 @@ struct SolveLaunch {
 };
 // CTAs and rows per CTA the QR kernel will use for (d, n); 0 CTAs if unsupported.
 int32_t solve_ctas(int64_t d, int64_t n, int32_t sms, size_t smem_optin);
+// Rows one QR launch can hold in shared memory for n columns (0 if n is unsupported).
+int64_t solve_rows_cap(int64_t n, int32_t sms, size_t smem_optin);
 cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launches);
 
 // Sketch-and-precondition LSQR (sk_lsqr.cu). Device scalars (FP64) of the recurrence:

@@ -4,7 +4,10 @@
 //
 // One cooperative launch factors W = [SA | Sb] (d x (n+1)) by Householder reflections. The d rows
 // are split across the CTAs (one per SM at most); each CTA keeps its rows of W in shared memory
-// for the whole factorization. Column step j needs one grid-wide reduction: the partial sums of
+// for the whole factorization. A sketch too tall for the GPU's shared memory is factored as a tree
+// (TSQR): groups of rows are factored by separate launches, their n x (n+1) factors [R_g | c_g] are
+// stacked in FP64 and factored again, until one launch holds the whole stack. Dropping each group's
+// last row (its residual norm) only removes a constant from ||W x~||, so the minimizer is unchanged. Column step j needs one grid-wide reduction: the partial sums of
 // x^T x and x^T W[:, c] (x = column j below the diagonal) give both the reflector and v^T W[:, c],
 // accumulated with FP64 atomics into per-step buffers, followed by one grid synchronization. The owner of row j
 // publishes that row before the barrier; after the last step every owner writes its final rows of R
@@ -27,7 +30,7 @@ namespace sk {
 namespace {
 
 // Columns of W = [SA | Sb] the kernel handles (n + 1 <= kQRMaxCols).
-constexpr int kQRMaxCols = 520;
+constexpr int kQRMaxCols = 1032;
 
 // A grid barrier gives up after about two seconds of waiting (in SM clock cycles at ~2 GHz).
 constexpr long long kBarrierCycles = 4000000000ll;
@@ -95,7 +98,8 @@ struct QRArgs {
 
 template <typename T>
 __device__ __forceinline__ double load_val(const void* p, int64_t idx) {
-  if constexpr (std::is_same<T, __half>::value) return (double)__half2float(reinterpret_cast<const __half*>(p)[idx]);
+  if constexpr (std::is_same<T, double>::value) return reinterpret_cast<const double*>(p)[idx];
+  else if constexpr (std::is_same<T, __half>::value) return (double)__half2float(reinterpret_cast<const __half*>(p)[idx]);
   else if constexpr (std::is_same<T, __nv_bfloat16>::value)
     return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[idx]);
   else return (double)reinterpret_cast<const float*>(p)[idx];
@@ -117,7 +121,7 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
   for (int64_t e = threadIdx.x; e < nown * ldw; e += blockDim.x) {
     const int64_t rl = e / ldw, c = e - rl * ldw;
     const int64_t r = row0 + rl;
-    Wl[e] = (c < n) ? load_val<T>(L.SA, r * n + c) : load_val<T>(L.Sb, r);
+    Wl[e] = (c < n) ? load_val<T>(L.SA, r * L.lda_sa + c) : load_val<T>(L.Sb, r * L.sb_stride);
   }
   __syncthreads();
   for (int64_t j = 0; j < n; ++j) {
@@ -177,6 +181,12 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
     const int64_t rl = jr - row0;
     for (int64_t c = jr + threadIdx.x; c <= n; c += blockDim.x) L.R[jr * ldw + c] = Wl[rl * ldw + c];
   }
+  // A group of a tree level: the rows of [R | c] are its whole output (below the diagonal stays 0).
+  if (!L.solve_x) {
+    for (int64_t jr = row0; jr < row0 + nown && jr < n; ++jr)
+      for (int64_t c = threadIdx.x; c < jr; c += blockDim.x) L.R[jr * ldw + c] = 0.0;
+    return;
+  }
   if (!grid_arrive_wait(L.bar, nb * (unsigned)(n + 2), L.status)) return;
   if (b != 0) return;
   // Back substitution on CTA 0 (column-oriented): rhs in shared memory (reuses Wl).
@@ -213,11 +223,22 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
   }
 }
 
+// Dynamic shared memory a QR CTA may use: the opt-in limit less the static arrays and a margin.
+size_t solve_smem_budget(size_t smem_optin) {
+  const size_t fixed = sizeof(double) * (kQRMaxCols + 32 + 4) + 2048;
+  return smem_optin > fixed ? smem_optin - fixed : 0;
+}
+
 }  // namespace
+
+int64_t solve_rows_cap(int64_t n, int32_t sms, size_t smem_optin) {
+  if (n < 1 || n + 1 > kQRMaxCols) return 0;
+  return (int64_t)sms * (int64_t)(solve_smem_budget(smem_optin) / ((size_t)(n + 1) * 8));
+}
 
 int32_t solve_ctas(int64_t d, int64_t n, int32_t sms, size_t smem_optin) {
   if (n < 1 || d < n || n + 1 > kQRMaxCols) return 0;
-  const size_t budget = smem_optin > 10240 ? smem_optin - 10240 : 0;  // static shared memory and margin
+  const size_t budget = solve_smem_budget(smem_optin);
   int64_t ncta = std::min<int64_t>(sms, std::max<int64_t>(1, (d + 7) / 8));
   for (; ncta <= sms; ++ncta) {
     const int64_t rpc = (d + ncta - 1) / ncta;
@@ -239,7 +260,8 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launche
   if (e != cudaSuccess) return e;
   const size_t smem = std::max<size_t>((size_t)a.rpc * (size_t)(L.n + 1) * 8, (size_t)L.n * 8);
   void* args[] = {(void*)&a};
-  const void* kern = (L.rule == kFP32)   ? (const void*)qr64_kernel<float>
+  const void* kern = L.src_fp64          ? (const void*)qr64_kernel<double>
+                     : (L.rule == kFP32) ? (const void*)qr64_kernel<float>
                      : (L.rule == kBF16) ? (const void*)qr64_kernel<__nv_bfloat16>
                                          : (const void*)qr64_kernel<__half>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

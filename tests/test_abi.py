@@ -42,4 +42,10 @@ def test_plan_validation_runs_without_gpu():
     h = sk.sk_plan_create(4096, 1 << 22, 8, sk.SK_FP16_RN, 7)
     sk.sk_plan_set(h, sk.SK_PARAM_CHUNK_ROWS, 4096)
     assert sk.sk_plan_get(h, sk.SK_PARAM_CHUNK_ROWS) == 4096
+    assert sk.sk_plan_get(h, sk.SK_PARAM_SOLVE_GROUP_ROWS) == 0
+    sk.sk_plan_set(h, sk.SK_PARAM_SOLVE_GROUP_ROWS, 96)
+    assert sk.sk_plan_get(h, sk.SK_PARAM_SOLVE_GROUP_ROWS) == 96
+    with pytest.raises(sk.SkError) as e:
+        sk.sk_plan_set(h, sk.SK_PARAM_SOLVE_GROUP_ROWS, -1)
+    assert e.value.status == sk.SK_ERR_INVALID_ARG
     sk.sk_destroy(h)
