@@ -41,7 +41,8 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "sweep_m4M_n64_d4096_k8"
 METRIC = "SA sketch HBM GB/s (% of peak) FP16 vs FP32 at equal distortion; p99 solve ms"
-KERNEL_SOURCES = ["paper_2606_20195_gb300/csrc/sk_tile.cuh", "paper_2606_20195_gb300/csrc/sk_kernels.cu",
+KERNEL_SOURCES = ["paper_2606_20195_gb300/csrc/sk_tile.cuh", "paper_2606_20195_gb300/csrc/sk_tile_kernel.cuh",
+                  "paper_2606_20195_gb300/csrc/sk_kernels.cu",
                   "paper_2606_20195_gb300/csrc/sk_own.cu",
                   "paper_2606_20195_gb300/csrc/sk_device.cuh"]
 
@@ -272,19 +273,24 @@ def coherence_of(U) -> float:
     return float((U.double() ** 2).sum(dim=1).max()) * m / n
 
 
+# nonzeros per column of SparseStack in the paper's experiments (Sec. 5, "unless otherwise stated")
+ZETA = 4
+
+
 def bench_paper(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 32, 64, 128, 256),
                 sweep_ratios=(2, 4, 8, 16), alphas=(0.0, 0.3, 0.6, 0.8, 0.9, 0.95, 1.0), reps=3):
     """The paper's sketching experiments on synthetic inputs (Sec. 5.1-5.2): distortion eta and
     throughput over the sketch ratio d/n for a Gaussian and an identity-like orthonormal basis
     U (m x n), and the coherence sweep U(alpha) = orth((1 - alpha) Q_rand + alpha [I; 0]).
-    SparseStack (k = 8) with every rounding rule and CountSketch (k = 1); U itself is the sketched
-    matrix (its GB/s is the throughput). Inputs are built with torch (FP32 QR), not by the library."""
+    SparseStack (k = 4, the paper's default) with every rounding rule and CountSketch (k = 1); U itself
+    is the sketched matrix (its GB/s is the throughput); throughput also at m = 2^19 and 2^20. Inputs
+    are built with torch (FP32 QR), not by the library."""
     import torch
     from paper_2606_20195_gb300 import sk
     torch.backends.cuda.matmul.allow_tf32 = False
     g = torch.Generator(device=dev)
     g.manual_seed(2606)
-    methods = [("sparsestack", 8, r) for r in ("fp32", "fp16_rn", "fp16_sr", "fp16_dither", "bf16_rn")]
+    methods = [("sparsestack", ZETA, r) for r in ("fp32", "fp16_rn", "fp16_sr", "fp16_dither", "bf16_rn")]
     methods += [("countsketch", 1, "fp32"), ("countsketch", 1, "fp16_rn")]
 
     def sketch(U, d, k, rule_name, timed=False):
@@ -308,7 +314,7 @@ def bench_paper(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 32, 64, 128, 256),
         plan.close()
         return Y.float(), ms
 
-    out = {"workload": f"n={n} m={m}, d/n in {list(ratios)}; SparseStack k=8, CountSketch k=1", "extremes": {}}
+    out = {"workload": f"n={n} m={m}, d/n in {list(ratios)}; SparseStack k={ZETA}, CountSketch k=1", "extremes": {}}
     Qg = torch.linalg.qr(torch.randn((m, n), generator=g, device=dev)).Q.contiguous()
     Qc = torch.zeros((m, n), device=dev)
     Qc[:n] = torch.eye(n, device=dev)
@@ -343,6 +349,37 @@ def bench_paper(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 32, 64, 128, 256),
                 del Y
         del U
     out["coherence_sweep"] = sweep
+    # throughput at the paper's other leading dimensions (rows of the Gaussian basis)
+    tp = {}
+    for mm in (1 << 19, 1 << 20):
+        Um = Qg[:mm].contiguous()
+        row = {}
+        for name, k, rname in methods:
+            if rname not in ("fp32", "fp16_rn"):
+                continue
+            gbs = []
+            for r in ratios:
+                d = r * n
+                plan = sk.Plan(d, mm, k, sk.RULES[rname], seed=77)
+                Y = torch.empty((d, n), dtype=y_dtype(sk.RULES[rname]), device=dev)
+                for _ in range(2):
+                    plan.apply(Um, Y)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(reps):
+                    plan.apply(Um, Y)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                es = 4 if rname == "fp32" else 2
+                gbs.append((mm * n * 4 + d * n * es) / (ms * 1e-3) / 1e9)
+                plan.close()
+                del Y
+            row[f"{name}_{rname}"] = gbs
+        tp[str(mm)] = row
+        del Um
+    out["throughput_GBps_by_m"] = tp
     del Qg, Qc
     torch.cuda.empty_cache()
     return out
@@ -361,7 +398,7 @@ def bench_paper_ls(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 24), reps=2):
     torch.backends.cuda.matmul.allow_tf32 = False
     g = torch.Generator(device=dev)
     g.manual_seed(5303)
-    methods = [("sparsestack", 8, r) for r in ("fp32", "fp16_rn", "fp16_sr", "fp16_dither", "bf16_rn")]
+    methods = [("sparsestack", ZETA, r) for r in ("fp32", "fp16_rn", "fp16_sr", "fp16_dither", "bf16_rn")]
     methods += [("countsketch", 1, "fp32"), ("countsketch", 1, "fp16_rn")]
     step = 1 << 18
 
@@ -400,7 +437,7 @@ def bench_paper_ls(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 24), reps=2):
         perm = torch.randperm(m, generator=g, device=dev)
         yield "coherent_permuted", A[perm].contiguous(), b[perm].contiguous()
 
-    out = {"workload": f"m={m} n={n}, d/n in {list(ratios)}; SparseStack k=8, CountSketch k=1", "families": {}}
+    out = {"workload": f"m={m} n={n}, d/n in {list(ratios)}; SparseStack k={ZETA}, CountSketch k=1", "families": {}}
     for name, A, b in problems():
         fam = {"optimum_rel_res": optimum(A, b)}
         for r in ratios:
@@ -408,7 +445,7 @@ def bench_paper_ls(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 24), reps=2):
             row = {}
             # the paper's per-element scheme (R = 1, one FP16 atomic per contribution) beside the
             # chunked one, on the coherent problem at the two smallest ratios
-            extra = [("sparsestack_literal", 8, "fp16_rn")] if name.startswith("coherent") and r <= 4 else []
+            extra = [("sparsestack_literal", ZETA, "fp16_rn")] if name.startswith("coherent") and r <= 4 else []
             for meth, k, rname in methods + extra:
                 params = {"kernel": sk.SK_KERNEL_LITERAL, "chunk_rows": 1} if meth.endswith("literal") else {}
                 plan = sk.Plan(d, m, k, sk.RULES[rname], seed=31, **params)
@@ -638,6 +675,27 @@ def main() -> int:
                               "ms": statistics.mean(per)}
             etas[name] = Yv.double().cpu().numpy()
             p2.close()
+        # 16-bit A (sk_apply_typed): the same rows, half the bytes of A read; GB/s of its own
+        # algorithmic bytes (2 bytes per element of A).
+        for a_name, a_dt, a_code in (("fp16_rn_a_fp16", torch.float16, sk.SK_A_FP16),
+                                     ("fp16_rn_a_bf16", torch.bfloat16, sk.SK_A_BF16)):
+            A16 = A.to(a_dt)
+            p2 = sk.Plan(d, m, k, sk.SK_FP16_RN, seed=1234)
+            Y16 = torch.empty((d, n), dtype=torch.float16, device=dev)
+            for _ in range(3):
+                sk.sk_apply_typed(p2.handle, A16, a_code, n, n, Y16, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(5):
+                sk.sk_apply_typed(p2.handle, A16, a_code, n, n, Y16, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms16 = e0.elapsed_time(e1) / 5
+            variants[a_name] = {"GB/s": (m * n * 2 + d * n * 2) / (ms16 * 1e-3) / 1e9, "ms": ms16,
+                                "rows_per_s_vs_fp32_A": variants["fp16_rn"]["ms"] / ms16}
+            p2.close()
+            del A16, Y16
         # Distortion eta(S, Q) of the column space of A (A = Q R_A) for every rule (same S).
         import oracle
         R_A = oracle.tall_r_factor(A_h)

@@ -143,6 +143,25 @@ SK_API sk_status sk_plan_get(sk_plan plan, int32_t key, int64_t* value);
  */
 SK_API sk_status sk_apply(sk_plan plan, const float* A_dev, int64_t lda, int64_t n, void* Y_dev, void* stream);
 
+/* Element types of A for sk_apply_typed. */
+enum { SK_A_FP32 = 0, SK_A_FP16 = 1, SK_A_BF16 = 2 };
+
+/*
+ * sk_apply_typed — Y_dev = S * A_dev for A stored as FP32, binary16 or bfloat16 (a_type one of
+ * SK_A_FP32, SK_A_FP16, SK_A_BF16). 16-bit inputs move half the bytes of A; every value is converted
+ * exactly to FP32 as it is loaded, so the result is that of sk_apply on the FP32 copy of A (bit for
+ * bit in SK_MODE_DETERMINISTIC and SK_MODE_SERIAL_TILE). The paper's scheme reads FP32 A and names
+ * lower-precision formats only for the accumulation (Sec. 4.2); this entry point extends the input.
+ *   A_dev  device, m x n elements of a_type with row stride lda (>= n), aligned to the element
+ *          size; TMA staging needs a 16-byte-aligned A_dev and lda * element size a multiple of 16
+ *          (other layouts are accepted and run slower)
+ *   n, Y_dev, stream: as for sk_apply.
+ * Errors: SK_ERR_INVALID_ARG for an unknown a_type or a misaligned A_dev; SK_ERR_UNSUPPORTED with
+ * SK_KERNEL_OWNER and a 16-bit A (the owner kernel reads FP32 only).
+ */
+SK_API sk_status sk_apply_typed(sk_plan plan, const void* A_dev, int32_t a_type, int64_t lda, int64_t n, void* Y_dev,
+                                void* stream);
+
 /*
  * sk_apply_host — the same result from HOST buffers: A_host is copied to the device in row tiles
  * (pinned memory gives overlapped asynchronous copies; pageable memory is accepted), the tiles are

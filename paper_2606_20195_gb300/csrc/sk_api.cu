@@ -115,10 +115,10 @@ int64_t default_chunk_rows(int64_t m) {
   return ((R + 31) / 32) * 32;
 }
 
-// Whether A (device pointer, row stride lda) can be staged through TMA: 16-byte-aligned base and a
-// row stride that is a multiple of 16 bytes.
-bool tma_layout_ok(const void* A, int64_t lda) {
-  return (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && (lda & 3) == 0;
+// Whether A (device pointer, row stride lda, es-byte elements) can be staged through TMA: a
+// 16-byte-aligned base and a row stride that is a multiple of 16 bytes.
+bool tma_layout_ok(const void* A, int64_t lda, int64_t es = 4) {
+  return (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && (lda * es) % 16 == 0;
 }
 
 // Split each chunk into slices: at least about 4 work items per resident CTA, slices at least
@@ -312,13 +312,15 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
   return SK_OK;
 }
 
-sk_status validate_apply(const sk_plan_s* p, const void* A, int64_t lda, int64_t n, const void* Y) {
+sk_status validate_apply(const sk_plan_s* p, const void* A, int64_t lda, int64_t n, const void* Y,
+                         uintptr_t a_align = 4) {
   if (!p) return set_error(SK_ERR_INVALID_ARG, "plan is NULL");
   if (!A) return set_error(SK_ERR_INVALID_ARG, "A is NULL");
   if (!Y) return set_error(SK_ERR_INVALID_ARG, "Y is NULL");
   if (n < 1 || n > kMaxN) return set_error(SK_ERR_INVALID_ARG, "n=%lld outside [1, %lld]", (long long)n, (long long)kMaxN);
   if (lda < n) return set_error(SK_ERR_INVALID_ARG, "lda=%lld < n=%lld", (long long)lda, (long long)n);
-  if ((reinterpret_cast<uintptr_t>(A) & 3u) != 0) return set_error(SK_ERR_INVALID_ARG, "A must be 4-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(A) & (a_align - 1)) != 0)
+    return set_error(SK_ERR_INVALID_ARG, "A must be %d-byte aligned", (int)a_align);
   if ((reinterpret_cast<uintptr_t>(Y) & 3u) != 0) return set_error(SK_ERR_INVALID_ARG, "Y must be 4-byte aligned");
   if (p->m > (int64_t)1 << 40 || lda > ((int64_t)1 << 40) / std::max<int64_t>(p->m, 1))
     return set_error(SK_ERR_UNSUPPORTED, "A larger than 2^40 elements");
@@ -326,9 +328,10 @@ sk_status validate_apply(const sk_plan_s* p, const void* A, int64_t lda, int64_t
 }
 
 // Enqueue Y = S * A for rows [row_begin, row_begin + rows) (A row 0 = row_begin) with chunk rows R.
-// Y must already be zero.
-sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, int64_t row_begin, int64_t rows, void* Y,
-                         int64_t R_fixed, cudaStream_t st, int32_t* launches, int64_t* R_used, int64_t col_off = 0) {
+// Y must already be zero. a_type: element type of A (SK_A_FP32, SK_A_FP16, SK_A_BF16).
+sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, int64_t row_begin, int64_t rows, void* Y,
+                         int64_t R_fixed, cudaStream_t st, int32_t* launches, int64_t* R_used, int64_t col_off = 0,
+                         int32_t a_type = SK_A_FP32) {
   DevInfo di;
   sk_status s = dev_info(&di);
   if (s != SK_OK) return s;
@@ -355,6 +358,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
     }
     DetLaunch L;
     L.A = A;
+    L.a_type = a_type;
     L.Y = Y;
     L.P = p->det_P;
     L.lda = lda;
@@ -378,6 +382,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
     if (p->R > 1 || R_fixed > 1) return set_error(SK_ERR_INVALID_ARG, "the literal kernel implements chunk rows R = 1 only");
     LiteralLaunch L;
     L.A = A;
+    L.a_type = a_type;
     L.Y = Y;
     L.lda = lda;
     L.n = n;
@@ -396,11 +401,13 @@ sk_status enqueue_sketch(sk_plan_s* p, const float* A, int64_t lda, int64_t n, i
     return SK_OK;
   }
   TileCfg cfg;
-  s = choose_tile(p, n, rows, di, &cfg, tma_layout_ok(A, lda));
+  s = choose_tile(p, n, rows, di, &cfg, tma_layout_ok(A, lda, a_type == SK_A_FP32 ? 4 : 2));
   if (s != SK_OK) return s;
+  if (cfg.own && a_type != SK_A_FP32) return set_error(SK_ERR_UNSUPPORTED, "the owner kernel reads FP32 A only");
   if (R_fixed > 0) cfg.R = R_fixed;
   TileLaunch L;
   L.A = A;
+  L.a_type = a_type;
   L.Y = Y;
   L.lda = lda;
   L.n = n;
@@ -570,6 +577,23 @@ sk_status sk_apply(sk_plan p, const float* A, int64_t lda, int64_t n, void* Y, v
   if (e != cudaSuccess) return cuda_fail(e, "zeroing Y");
   int64_t R_used = 0;
   s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, Y, 0, st, &launches, &R_used);
+  p->last_launches = launches;
+  p->last_R = R_used;
+  return s;
+}
+
+sk_status sk_apply_typed(sk_plan p, const void* A, int32_t a_type, int64_t lda, int64_t n, void* Y, void* stream) {
+  clear_error();
+  if (a_type != SK_A_FP32 && a_type != SK_A_FP16 && a_type != SK_A_BF16)
+    return set_error(SK_ERR_INVALID_ARG, "unknown element type %d of A", a_type);
+  sk_status s = validate_apply(p, A, lda, n, Y, a_type == SK_A_FP32 ? 4 : 2);
+  if (s != SK_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t launches = 0;
+  cudaError_t e = cudaMemsetAsync(Y, 0, elem_size(p->rule) * (size_t)(p->d * n), st);
+  if (e != cudaSuccess) return cuda_fail(e, "zeroing Y");
+  int64_t R_used = 0;
+  s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, Y, 0, st, &launches, &R_used, 0, a_type);
   p->last_launches = launches;
   p->last_R = R_used;
   return s;

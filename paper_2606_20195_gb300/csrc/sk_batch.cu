@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchDesc* __restrict
     const BatchWork wk = work[w];
     if (threadIdx.x == 0) dsh = descs[wk.item];
     __syncthreads();
-    if (!tile_scatter(dsh.D, wk.r0, wk.r1, wk.g, wk.j0, wk.kbe, acc, wbuf, ring, warp, nwarps)) {
+    if (!tile_scatter_typed<float>(dsh.D, wk.r0, wk.r1, wk.g, wk.j0, wk.kbe, acc, wbuf, ring, warp, nwarps)) {
       abort_flag = 1;
       if (status) atomicOr(status, kStatusTimeout);
     }
@@ -224,6 +224,7 @@ sk_status build_batch(sk_batch_s* b) {
     slot_max = std::max(slot_max, ring_slot_bytes(RB * mb, NC));
     BatchDesc& D = descs[i];
     D.D.A = it.A_dev;
+    D.D.a_type = kAF32;
     D.D.Y = it.Y_dev;
     D.D.lda = it.lda;
     D.D.n = it.n;
@@ -302,7 +303,7 @@ sk_status build_batch(sk_batch_s* b) {
   for (int32_t i = 0; i < count; ++i) {
     memset(&maps[i], 0, sizeof(CUtensorMap));
     const sk_batch_item& it = b->items[i];
-    has_map[i] = encode_a_map(&maps[i], it.A_dev, it.lda, it.n, it.m, 1 << descs[i].D.log2NC,
+    has_map[i] = encode_a_map(&maps[i], it.A_dev, kAF32, it.lda, it.n, it.m, 1 << descs[i].D.log2NC,
                               (32 / ((it.k + 1) / 2)) * descs[i].D.mb)
                      ? 1
                      : 0;

@@ -10,6 +10,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace sk {
 
 // ------------------------------------------------------------------ SplitMix64
@@ -46,6 +48,32 @@ __device__ __forceinline__ uint32_t block_word(uint64_t bits, uint32_t j) {
 // Row offset inside block j (0 <= s < B) from the block's word: Lemire's multiply-shift,
 // floor(w * B / 2^32). Sign bit: bit 0 of the word (1 -> negative).
 __device__ __forceinline__ uint32_t word_to_slot(uint32_t w, uint32_t B) { return __umulhi(w, B); }
+
+// ------------------------------------------------------------------ element types of A
+// A arrives as FP32, binary16 or bfloat16; 16-bit values convert to FP32 exactly as they are read,
+// so the arithmetic after the load is the FP32 path's.
+enum AType { kAF32 = 0, kAF16 = 1, kABF16 = 2 };
+
+template <typename TA>
+__device__ __forceinline__ float a_to_f32(TA v) {
+  if constexpr (std::is_same<TA, __half>::value) return __half2float(v);
+  else if constexpr (std::is_same<TA, __nv_bfloat16>::value) return __bfloat162float(v);
+  else return v;
+}
+
+// Read-only load of one element of A (through the non-coherent cache) converted to FP32.
+template <typename TA>
+__device__ __forceinline__ float ld_a(const TA* p) {
+  if constexpr (std::is_same<TA, float>::value) return __ldg(p);
+  else return a_to_f32(__ldg(p));
+}
+
+// One element of A of run-time type `a_type` (slow paths: deterministic and literal kernels).
+__device__ __forceinline__ float ld_a_any(const void* A, int32_t a_type, int64_t idx) {
+  if (a_type == kAF16) return ld_a(static_cast<const __half*>(A) + idx);
+  if (a_type == kABF16) return ld_a(static_cast<const __nv_bfloat16*>(A) + idx);
+  return ld_a(static_cast<const float*>(A) + idx);
+}
 
 // ------------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11).

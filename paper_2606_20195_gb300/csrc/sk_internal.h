@@ -9,7 +9,8 @@ namespace sk {
 struct TileDesc;
 
 struct TileLaunch {
-  const float* A;
+  const void* A;    // elements of type a_type (0 FP32, 1 binary16, 2 bfloat16)
+  int32_t a_type = 0;
   void* Y;
   int64_t lda, n, row_begin, row_end;  // global rows [row_begin, row_end); A row 0 = row_begin
   int64_t d;
@@ -36,9 +37,11 @@ struct TileLaunch {
 
 // Shared-memory bytes the tile kernel needs for (B, kb, NC, threads, k, ring depth, rounds per box).
 size_t tile_smem_bytes(int64_t B, int32_t kb, int32_t NC, int32_t threads, int32_t k, int32_t depth, int32_t mb = 1);
-// Encode a 2-D tensor map over A (n columns, `rows` rows, row stride lda) with box NC x RB; false if
-// the layout does not allow TMA (A not 16-byte aligned, lda % 4 != 0, too many rows).
-bool encode_a_map(void* map, const float* A, int64_t lda, int64_t n, int64_t rows, int32_t NC, int32_t RB);
+// Encode a 2-D tensor map over A (n columns, `rows` rows, row stride lda, element type a_type) with box
+// NC x RB; false if the layout does not allow TMA (A not 16-byte aligned, row stride or box width not
+// a multiple of 16 bytes, too many rows).
+bool encode_a_map(void* map, const void* A, int32_t a_type, int64_t lda, int64_t n, int64_t rows, int32_t NC,
+                  int32_t RB);
 int32_t tile_slots(int32_t NC, int32_t kb);
 // Add the chunk totals of P (chunk-major, d x n FP32 each, chunks [t_first, t_first + chunks)) into
 // Y in ascending chunk order with the rule's scaling and rounding, and clear P (one launch).
@@ -58,7 +61,8 @@ void tile_geometry(const TileLaunch& L, int64_t* chunks, int32_t* ncg, int32_t* 
 int32_t tile_ctas_per_sm(int32_t rule, int32_t threads, size_t smem);
 
 struct LiteralLaunch {
-  const float* A;
+  const void* A;
+  int32_t a_type = 0;
   void* Y;
   int64_t lda, n, row_begin, row_end, d;
   int32_t k, rule;
@@ -69,7 +73,8 @@ struct LiteralLaunch {
 cudaError_t launch_literal(const LiteralLaunch& L, cudaStream_t st, int32_t* launches);
 
 struct DetLaunch {
-  const float* A;
+  const void* A;
+  int32_t a_type = 0;
   void* Y;
   float* P;  // d x n FP32 scratch, zeroed by the launcher
   int64_t lda, n, row_begin, row_end, d;

@@ -10,55 +10,17 @@
 #include "sk_device.cuh"
 #include "sk_internal.h"
 #include "sk_tile.cuh"
+#include "sk_tile_kernel.cuh"
 
 namespace sk {
 
-// ------------------------------------------------------------------ tile kernel
-
-template <int RULE>
-__global__ void __launch_bounds__(1024) tile_kernel(const TileGrid P, const __grid_constant__ CUtensorMap tmap) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ int abort_flag;
-  float* acc = reinterpret_cast<float*>(smem_raw);
-  const int warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  const int RBh = 32 / (int)P.D.kp;
-  const SmemPlan SL = smem_plan(P.acc_floats, nwarps, ring_slot_bytes(RBh * P.D.mb, 1 << P.D.log2NC), P.depth);
-  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem_raw + SL.wbuf_off) + warp * kWordsPerWarp;
-  WarpRing ring = make_ring(smem_raw, SL, warp);
-  for (int x = threadIdx.x; x < P.acc_floats; x += blockDim.x) acc[x] = 0.f;
-  if (threadIdx.x == 0) abort_flag = 0;
-  __syncthreads();
-  TileDesc D = P.D;
-  D.tmap = P.use_tma ? (const void*)&tmap : nullptr;
-  const int64_t dn = (int64_t)D.B * D.k * D.n;
-  for (int64_t w = blockIdx.x; w < P.items; w += gridDim.x) {
-    const int32_t g = (int32_t)(w % P.ncg);
-    int64_t rest = w / P.ncg;
-    const int32_t bg = (int32_t)(rest % P.nbg);
-    rest /= P.nbg;
-    const int32_t sl = (int32_t)(rest % P.slices);
-    const int64_t tl = rest / P.slices;
-    const int64_t t = P.t_first + tl;
-    const int64_t c0 = max(t * P.R, P.row_begin);
-    const int64_t c1 = min((t + 1) * P.R, P.row_end);
-    const int64_t r0 = c0 + (c1 - c0) * sl / P.slices;
-    const int64_t r1 = c0 + (c1 - c0) * (sl + 1) / P.slices;
-    const int32_t j0 = bg * D.kb;
-    const int32_t kbe = min(D.kb, (int32_t)D.k - j0);
-    if (!tile_scatter(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps)) {
-      abort_flag = 1;
-      if (P.status) atomicOr(P.status, kStatusTimeout);
-    }
-    __syncthreads();
-    if (abort_flag) break;
-    if (P.slices == 1) {
-      tile_flush<RULE>(D, t, g, j0, kbe, acc);
-    } else {
-      // slice partials into the chunk totals; chunk_finish_kernel adds them into Y after this launch
-      tile_flush_partial(D, g, j0, kbe, acc, P.P + tl * dn);
-    }
-    __syncthreads();
+static TileKernelFn tile_kernel_f32(int32_t rule) {
+  switch (rule) {
+    case kRN: return tile_kernel<kRN, float>;
+    case kSR: return tile_kernel<kSR, float>;
+    case kDither: return tile_kernel<kDither, float>;
+    case kBF16: return tile_kernel<kBF16, float>;
+    default: return tile_kernel<kFP32, float>;
   }
 }
 
@@ -86,17 +48,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-bool encode_a_map(void* map, const float* A, int64_t lda, int64_t n, int64_t rows, int32_t NC, int32_t RB) {
-  if ((reinterpret_cast<uintptr_t>(A) & 15u) != 0 || (lda & 3) != 0 || rows >= ((int64_t)1 << 31) ||
-      n >= ((int64_t)1 << 31) || RB > 256 || NC > 256)
+bool encode_a_map(void* map, const void* A, int32_t a_type, int64_t lda, int64_t n, int64_t rows, int32_t NC,
+                  int32_t RB) {
+  const int64_t es = (a_type == kAF32) ? 4 : 2;
+  // 16-byte-aligned base, row stride and box width (the box width rule: NC * es a multiple of 16)
+  if ((reinterpret_cast<uintptr_t>(A) & 15u) != 0 || (lda * es) % 16 != 0 || ((int64_t)NC * es) % 16 != 0 ||
+      rows >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31) || RB > 256 || NC > 256)
     return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)lda * 4};
+  const cuuint64_t strides[1] = {(cuuint64_t)(lda * es)};
   const cuuint32_t box[2] = {(cuuint32_t)NC, (cuuint32_t)RB};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = enc(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)A, dims,
+  const CUtensorMapDataType dt = (a_type == kAF16)    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : (a_type == kABF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUresult r = enc(reinterpret_cast<CUtensorMap*>(map), dt, 2, (void*)A, dims,
                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -123,6 +91,7 @@ void tile_geometry(const TileLaunch& L, int64_t* chunks, int32_t* ncg, int32_t* 
 // quad into the chunk total P[t - t_first][target][...] with one red.global.add.v4.f32 (scalar FP32
 // reductions for a ragged last quad or n % 4 != 0). Contributions reach each chunk total in any order
 // (atomic mode); chunk_finish_kernel then adds the totals into Y in chunk order.
+template <typename TA>
 __global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P, int64_t row_end, int64_t R,
                                                      int64_t t_first) {
   const int lane = threadIdx.x & 31;
@@ -132,10 +101,12 @@ __global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P,
   const int64_t nq = (n + 3) >> 2;
   const int k = (int)D.k;
   const int64_t dn = (int64_t)D.B * D.k * n;
-  const bool vec = (n & 3) == 0 && (D.lda & 3) == 0 && (reinterpret_cast<uintptr_t>(D.A) & 15u) == 0;
+  // quads of A in one vector load: 16 bytes of FP32 or 8 bytes of 16-bit values
+  const bool vec = (n & 3) == 0 && (D.lda & 3) == 0 &&
+                   (reinterpret_cast<uintptr_t>(D.A) & (std::is_same<TA, float>::value ? 15u : 7u)) == 0;
   for (int64_t i = D.row_base + wg; i < row_end; i += nw) {
     float* Pt = P + (i / R - t_first) * dn;
-    const float* arow = D.A + (i - D.row_base) * D.lda;
+    const TA* arow = static_cast<const TA*>(D.A) + (i - D.row_base) * D.lda;
     for (int jb = 0; jb < k; jb += 32) {
       // this lane's block jb + lane: target row (with the block offset) and sign bit
       uint32_t tw = 0;
@@ -152,12 +123,18 @@ __global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P,
         const int64_t col0 = 4 * q;
         if (active) {
           if (vec) {
-            a = __ldg(reinterpret_cast<const float4*>(arow + col0));
+            if constexpr (std::is_same<TA, float>::value) {
+              a = __ldg(reinterpret_cast<const float4*>(arow + col0));
+            } else {
+              const uint2 u = __ldg(reinterpret_cast<const uint2*>(arow + col0));
+              const TA* h = reinterpret_cast<const TA*>(&u);
+              a = make_float4(a_to_f32(h[0]), a_to_f32(h[1]), a_to_f32(h[2]), a_to_f32(h[3]));
+            }
           } else {
-            a.x = __ldg(arow + col0);
-            if (col0 + 1 < n) a.y = __ldg(arow + col0 + 1);
-            if (col0 + 2 < n) a.z = __ldg(arow + col0 + 2);
-            if (col0 + 3 < n) a.w = __ldg(arow + col0 + 3);
+            a.x = ld_a(arow + col0);
+            if (col0 + 1 < n) a.y = ld_a(arow + col0 + 1);
+            if (col0 + 2 < n) a.z = ld_a(arow + col0 + 2);
+            if (col0 + 3 < n) a.w = ld_a(arow + col0 + 3);
           }
         }
         for (int jj = 0; jj < kk; ++jj) {
@@ -201,6 +178,7 @@ cudaError_t launch_global(const TileLaunch& L, cudaStream_t st, int32_t* launche
   D.S = 1;
   D.kb = L.k;
   D.col_off = L.col_off;
+  D.a_type = L.a_type;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -209,7 +187,11 @@ cudaError_t launch_global(const TileLaunch& L, cudaStream_t st, int32_t* launche
   const int64_t rows = L.row_end - L.row_begin;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, (int64_t)sms * 8));
   const int64_t t_first = L.row_begin / L.R;
-  global_kernel<<<(unsigned)grid, 256, 0, st>>>(D, L.P, L.row_end, L.R, t_first);
+  switch (L.a_type) {
+    case kAF16: global_kernel<__half><<<(unsigned)grid, 256, 0, st>>>(D, L.P, L.row_end, L.R, t_first); break;
+    case kABF16: global_kernel<__nv_bfloat16><<<(unsigned)grid, 256, 0, st>>>(D, L.P, L.row_end, L.R, t_first); break;
+    default: global_kernel<float><<<(unsigned)grid, 256, 0, st>>>(D, L.P, L.row_end, L.R, t_first); break;
+  }
   if (launches) *launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -247,13 +229,15 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   P.P = L.P;
   P.status = L.status;
   P.D.col_off = L.col_off;
+  P.D.a_type = L.a_type;
   P.D.tmap = nullptr;
   if (P.slices > 1 && !P.P) return cudaErrorInvalidValue;
   CUtensorMap tmap;
   memset(&tmap, 0, sizeof(tmap));
   const int32_t RB = 32 / (int32_t)P.D.kp;
   P.D.mb = std::max(1, L.mb);
-  P.use_tma = (L.allow_tma && encode_a_map(&tmap, L.A, L.lda, L.n, L.row_end - L.row_begin, L.NC, RB * P.D.mb)) ? 1 : 0;
+  P.use_tma = (L.allow_tma &&
+                encode_a_map(&tmap, L.A, L.a_type, L.lda, L.n, L.row_end - L.row_begin, L.NC, RB * P.D.mb)) ? 1 : 0;
   P.D.lr = (P.use_tma && L.lr && L.kb == L.k) ? 1 : 0;
   P.D.vec = (L.vec && L.n == 1 && L.NC == 4) ? 1 : 0;
   if (P.D.vec) {
@@ -268,14 +252,8 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  void (*kern)(const TileGrid, const CUtensorMap);
-  switch (L.rule) {
-    case kRN: kern = tile_kernel<kRN>; break;
-    case kSR: kern = tile_kernel<kSR>; break;
-    case kDither: kern = tile_kernel<kDither>; break;
-    case kBF16: kern = tile_kernel<kBF16>; break;
-    default: kern = tile_kernel<kFP32>; break;
-  }
+  const TileKernelFn kern = (L.a_type == kAF32) ? tile_kernel_f32(L.rule) : tile_kernel_a16(L.rule, L.a_type);
+  if (!kern) return cudaErrorInvalidValue;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -322,14 +300,7 @@ cudaError_t launch_chunk_finish(const TileDesc& D, int32_t rule, float* P, int64
 }
 
 int32_t tile_ctas_per_sm(int32_t rule, int32_t threads, size_t smem) {
-  void (*kern)(const TileGrid, const CUtensorMap);
-  switch (rule) {
-    case kRN: kern = tile_kernel<kRN>; break;
-    case kSR: kern = tile_kernel<kSR>; break;
-    case kDither: kern = tile_kernel<kDither>; break;
-    case kBF16: kern = tile_kernel<kBF16>; break;
-    default: kern = tile_kernel<kFP32>; break;
-  }
+  const TileKernelFn kern = tile_kernel_f32(rule);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -359,8 +330,8 @@ __global__ void literal_kernel(const LiteralLaunch L, uint32_t B, uint32_t kp) {
     const int64_t c0 = 2 * (tid - il * ncp);
     const int64_t i = L.row_begin + il;
     const bool has1 = c0 + 1 < n;
-    const float a0 = __ldg(L.A + il * L.lda + c0);
-    const float a1 = has1 ? __ldg(L.A + il * L.lda + c0 + 1) : 0.f;
+    const float a0 = ld_a_any(L.A, L.a_type, il * L.lda + c0);
+    const float a1 = has1 ? ld_a_any(L.A, L.a_type, il * L.lda + c0 + 1) : 0.f;
     uint64_t bits = 0;
     for (uint32_t j = 0; j < (uint32_t)L.k; ++j) {
       if ((j & 1u) == 0) bits = row_pair_bits(L.seed, (uint64_t)i, kp, j >> 1);
@@ -440,7 +411,7 @@ __global__ void det_kernel(const DetLaunch L, uint32_t B, uint32_t kp) {
     for (int64_t i = r0; i < r1; ++i) {
       const uint32_t w = block_word(row_pair_bits(L.seed, (uint64_t)i, kp, j >> 1), j);
       const int64_t r = (int64_t)j * B + word_to_slot(w, B);
-      const float a = L.A[(i - L.row_begin) * L.lda + c];
+      const float a = ld_a_any(L.A, L.a_type, (i - L.row_begin) * L.lda + c);
       float* p = L.P + r * n + c;
       *p = __fadd_rn(*p, (w & 1u) ? -a : a);
     }

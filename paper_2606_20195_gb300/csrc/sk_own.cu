@@ -235,7 +235,8 @@ int32_t own_ctas_per_sm(int32_t rule, size_t smem) {
 }
 
 cudaError_t launch_own(const TileLaunch& L, cudaStream_t st, int32_t* launches) {
-  if (L.NC != 32 || L.kb < 1 || L.kb > 2) return cudaErrorInvalidValue;
+  // FP32 A only (its staging and consumer loads are written for 4-byte elements)
+  if (L.NC != 32 || L.kb < 1 || L.kb > 2 || L.a_type != kAF32) return cudaErrorInvalidValue;
   TileGrid P;
   memset(&P, 0, sizeof(P));
   const int64_t B = L.d / L.k;
@@ -272,7 +273,8 @@ cudaError_t launch_own(const TileLaunch& L, cudaStream_t st, int32_t* launches) 
   if (P.slices > 1 && !P.P) return cudaErrorInvalidValue;
   CUtensorMap tmap;
   memset(&tmap, 0, sizeof(tmap));
-  if (!encode_a_map(&tmap, L.A, L.lda, L.n, L.row_end - L.row_begin, 32, kOwnStageRows)) return cudaErrorInvalidValue;
+  if (!encode_a_map(&tmap, L.A, kAF32, L.lda, L.n, L.row_end - L.row_begin, 32, kOwnStageRows))
+    return cudaErrorInvalidValue;
   P.use_tma = 1;
   const size_t smem = own_smem((int64_t)P.acc_floats).total;
   const OwnKernel kern = own_kernel_ptr(L.rule);

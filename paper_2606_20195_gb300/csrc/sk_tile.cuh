@@ -26,7 +26,7 @@
 namespace sk {
 
 struct TileDesc {
-  const float* A;   // row 0 of A is global row `row_base`
+  const void* A;    // row 0 of A is global row `row_base`; elements of type a_type
   void* Y;          // d x n, float or binary16
   int64_t lda;
   int64_t n;
@@ -44,6 +44,7 @@ struct TileDesc {
   int32_t mb;       // hash rounds (of RB = 32/kp rows) per TMA box
   int32_t lr;       // 1: every work item holds all k blocks and takes the lane-row TMA path
   int32_t vec;      // 1: n = 1, one thread per row (tile_scatter_vec)
+  int32_t a_type;   // element type of A (AType: FP32, binary16, bfloat16)
 };
 
 // Launch parameters of the chunked kernels (tile kernel and owner kernel).
@@ -130,7 +131,7 @@ __device__ __forceinline__ WarpRing make_ring(unsigned char* smem_raw, const Sme
 // With a tensor map, the warp's batches of A arrive through its TMA ring (ring.depth batches in
 // flight); otherwise each lane loads its batch's values directly. Returns false if a bounded wait
 // gave up (after waiting, again bounded, for the warp's copies still in flight).
-template <int PPR>
+template <int PPR, typename TA>
 __device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
                                                int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
                                                int nwarps) {
@@ -145,7 +146,7 @@ __device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, in
   const int kp = (int)D.kp;
   const int64_t col = (int64_t)g * NC + c;
   const bool col_ok = col < D.n;
-  const float* __restrict__ Abase = D.A + (col_ok ? col : 0);
+  const TA* __restrict__ Abase = static_cast<const TA*>(D.A) + (col_ok ? col : 0);
   float* __restrict__ acc_c = acc + c;
   // Rows of one batch: the 32 lanes compute one 64-bit stream output each, kp per row.
   const int RB = 32 / kp;
@@ -165,7 +166,7 @@ __device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, in
   }
   const bool tma = D.tmap != nullptr;
   const int depth = ring.depth;
-  const uint32_t box_bytes = (uint32_t)(RB * NC * 4);
+  const uint32_t box_bytes = (uint32_t)(RB * NC * sizeof(TA));
   auto issue = [&](int64_t kk) {
     const int64_t bt = warp + kk * nwarps;
     const uint32_t u = ring.uses + (uint32_t)kk;
@@ -195,7 +196,7 @@ __device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, in
       }
     }
     // Values of this batch: from the staging slot (row-major RB x NC box) or loaded directly.
-    const float* stage = nullptr;
+    const TA* stage = nullptr;
     if (tma) {
       const uint32_t u = ring.uses + (uint32_t)kk;
       const int slot = (int)(u % (uint32_t)depth);
@@ -208,7 +209,7 @@ __device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, in
         }
         break;
       }
-      stage = ring.slots + (size_t)slot * ring.slot_floats;
+      stage = reinterpret_cast<const TA*>(ring.slots + (size_t)slot * ring.slot_floats);
     }
     __syncwarp();
     // This lane's updates of the batch, enumerated as entries e = 0..E-1, processed in groups of 8
@@ -218,7 +219,7 @@ __device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, in
       // so their lanes add zeros into accumulator columns that are never flushed.
 #pragma unroll 2
       for (int rl = 0; rl < nr; ++rl) {
-        const float a = stage[rl * NC + c];
+        const float a = a_to_f32(stage[rl * NC + c]);
         const uint32_t* wr = wbuf + rl * kbe + q;
 #pragma unroll
         for (int pp = 0; pp < (PPR > 0 ? PPR : 1); ++pp) {
@@ -230,7 +231,7 @@ __device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, in
       }
     } else if (kbe >= G) {
       for (int rl = 0; rl < nr; ++rl) {
-        const float a = tma ? stage[rl * NC + c] : (col_ok ? __ldg(Abase + (ib + rl - D.row_base) * D.lda) : 0.f);
+        const float a = tma ? a_to_f32(stage[rl * NC + c]) : (col_ok ? ld_a(Abase + (ib + rl - D.row_base) * D.lda) : 0.f);
         const uint32_t* wr = wbuf + rl * kbe;
         for (int jl = q; jl < kbe; jl += G) {
           const uint32_t w = wr[jl];
@@ -245,7 +246,7 @@ __device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, in
       const int jl = q - roff * kbe;
       if (roff < RP && col_ok) {
         for (int rl = roff; rl < nr; rl += RP) {
-          const float a = tma ? stage[rl * NC + c] : __ldg(Abase + (ib + rl - D.row_base) * D.lda);
+          const float a = tma ? a_to_f32(stage[rl * NC + c]) : ld_a(Abase + (ib + rl - D.row_base) * D.lda);
           const uint32_t w = wbuf[rl * kbe + jl];
           const float v = __uint_as_float(__float_as_uint(a) ^ (w & 0x80000000u));
           atomicAdd(acc_c + (w & 0x7FFFFFFFu), v);
@@ -267,7 +268,7 @@ __device__ __forceinline__ bool tile_scatter_t(const TileDesc& D, int64_t r0, in
 // rows each; PPR (row, block) passes per row, unrolled. Slot and phase parity advance incrementally.
 // Columns past n read TMA zero fill, so those lanes add zeros into accumulator columns that are never
 // flushed. Returns false if a bounded wait gave up (after draining this warp's copies in flight).
-template <int PPR>
+template <int PPR, typename TA>
 __device__ __forceinline__ bool tile_scatter_tma(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
                                                  int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
                                                  int nwarps) {
@@ -298,7 +299,7 @@ __device__ __forceinline__ bool tile_scatter_tma(const TileDesc& D, int64_t r0, 
     hoff[e] = (hj[e] >= 0) ? (uint32_t)((jl / S) * (int)B * LW + (jl % S) * NC) : 0u;
   }
   const int depth = ring.depth;
-  const uint32_t box_bytes = (uint32_t)(SB * NC * 4);
+  const uint32_t box_bytes = (uint32_t)(SB * NC * sizeof(TA));
   const int32_t ybase = (int32_t)(r0 - D.row_base);
   const int xcol = g * NC;
   int slot = (int)(ring.uses % (uint32_t)depth);
@@ -326,7 +327,7 @@ __device__ __forceinline__ bool tile_scatter_tma(const TileDesc& D, int64_t r0, 
       }
       break;
     }
-    const float* stage = ring.slots + (size_t)slot * ring.slot_floats;
+    const TA* stage = reinterpret_cast<const TA*>(ring.slots + (size_t)slot * ring.slot_floats);
     for (int hb = 0; hb < D.mb; ++hb) {
       const int32_t rb0 = box0 + hb * RB;
       const int nr = min(RB, nrows - rb0);
@@ -342,10 +343,10 @@ __device__ __forceinline__ bool tile_scatter_tma(const TileDesc& D, int64_t r0, 
         }
       }
       __syncwarp();
-      const float* st = stage + hb * RB * NC + c;
+      const TA* st = stage + hb * RB * NC + c;
 #pragma unroll 2
       for (int rl = 0; rl < nr; ++rl) {
-        const float a = st[rl * NC];
+        const float a = a_to_f32(st[rl * NC]);
         const uint32_t* wr = wbuf + rl * kbe + q;
 #pragma unroll
         for (int pp = 0; pp < PPR; ++pp) {
@@ -380,8 +381,8 @@ __device__ __forceinline__ void red_shared_f32(uint32_t addr, float v) {
 // (target row and column still to add). PRED = false is the straight-line form for rounds in which
 // every lane holds a row and both its blocks exist.
 // `z` is the SplitMix64 state of the lane's stream output (seed + index * golden gamma).
-template <int NC, bool PRED>
-__device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int rot, int flip, const float* arow,
+template <int NC, bool PRED, typename TA>
+__device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int rot, int flip, const TA* arow,
                                          const uint32_t base[2], const bool bv[2], uint32_t LW) {
   const uint64_t h = splitmix_finalize(z);
   uint32_t ad[2], sg[2];
@@ -395,7 +396,7 @@ __device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int rot,
 #pragma unroll(NC > 16 ? 8 : NC)
   for (int c = 0; c < NC; ++c) {
     const uint32_t col = (uint32_t)(c + rot) & (uint32_t)(NC - 1);
-    const uint32_t a = __float_as_uint(arow[col]);
+    const uint32_t a = __float_as_uint(a_to_f32(arow[col]));
     if (!PRED || bv[0]) red_shared_f32(ad[0] + 4u * col, __uint_as_float(a ^ sg[0]));
     if (!PRED || bv[1]) red_shared_f32(ad[1] + 4u * col, __uint_as_float(a ^ sg[1]));
   }
@@ -413,7 +414,7 @@ __device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int rot,
 // from shared memory and no warp-level exchange is needed, so a round is straight-line code.
 // Boxes, ring and bounded waits are as in tile_scatter_tma. Columns past n read TMA zero fill and
 // add zeros into accumulator columns that are never flushed.
-template <int NC>
+template <int NC, typename TA>
 __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, float* acc,
                                                 WarpRing& ring, int warp, int nwarps) {
   const int lane = threadIdx.x & 31;
@@ -442,7 +443,7 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
   const int32_t nbox = (nrows + SB - 1) / SB;
   const int32_t nmine = (nbox > warp) ? (nbox - 1 - warp) / nwarps + 1 : 0;
   const int depth = ring.depth;
-  const uint32_t box_bytes = (uint32_t)(SB * NC * 4);
+  const uint32_t box_bytes = (uint32_t)(SB * NC * sizeof(TA));
   const int32_t ybase = (int32_t)(r0 - D.row_base);
   const int xcol = g * NC;
   int slot = (int)(ring.uses % (uint32_t)depth);
@@ -470,7 +471,7 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
       }
       break;
     }
-    const float* stage = ring.slots + (size_t)slot * ring.slot_floats;
+    const TA* stage = reinterpret_cast<const TA*>(ring.slots + (size_t)slot * ring.slot_floats);
     const int32_t nr_box = min(SB, nrows - box0);
     // Stream output index of (row, pair) = row * kp + hp + 1; the next round's is RB * kp further on.
     const uint64_t idx0 = (uint64_t)(r0 + box0 + r) * (uint64_t)kp + (uint64_t)hp + 1ull;
@@ -478,11 +479,11 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
     const uint64_t dz = (uint64_t)(RB * kp) * kSplitMixGamma;
     if (full_lanes && nr_box == SB) {
       for (int hb = 0; hb < D.mb; ++hb, z += dz)
-        lr_round<NC, false>(D, z, rot, flip, stage + (hb * RB + r) * NC, base, bv, LW);
+        lr_round<NC, false, TA>(D, z, rot, flip, stage + (hb * RB + r) * NC, base, bv, LW);
     } else {
       for (int hb = 0; hb < D.mb; ++hb, z += dz) {
         const int rr = hb * RB + r;  // row of the box
-        if (r < RB && rr < nr_box) lr_round<NC, true>(D, z, rot, flip, stage + rr * NC, base, bv, LW);
+        if (r < RB && rr < nr_box) lr_round<NC, true, TA>(D, z, rot, flip, stage + rr * NC, base, bv, LW);
       }
     }
     __syncwarp();
@@ -504,11 +505,13 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
 // r0 + tid, r0 + tid + blockDim, ... of the work item, loads the row's value (consecutive threads
 // read consecutive rows), evaluates the row's stream outputs for blocks j0 .. j0+kbe-1 and adds the
 // signed value into each block's target. Rows whose value is zero add nothing and are skipped.
+template <typename TA>
 __device__ __forceinline__ void tile_scatter_vec(const TileDesc& D, int64_t r0, int64_t r1, int32_t j0, int32_t kbe,
                                                  float* acc) {
   const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
+  const TA* A = static_cast<const TA*>(D.A);
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    const uint32_t a = __float_as_uint(__ldg(D.A + (i - D.row_base) * D.lda));
+    const uint32_t a = __float_as_uint(ld_a(A + (i - D.row_base) * D.lda));
     if ((a << 1) == 0u) continue;
     uint64_t h = 0;
     for (int jl = 0; jl < kbe; ++jl) {
@@ -523,12 +526,13 @@ __device__ __forceinline__ void tile_scatter_vec(const TileDesc& D, int64_t r0, 
 
 // Dispatch: the vector or lane-row path when the host set it up, else on the passes per row of the
 // work item (blocks per lane group) for the unrolled path.
-__device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
-                                             int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
-                                             int nwarps) {
+template <typename TA>
+__device__ __forceinline__ bool tile_scatter_typed(const TileDesc& D, int64_t r0, int64_t r1, int32_t g, int32_t j0,
+                                                   int32_t kbe, float* acc, uint32_t* wbuf, WarpRing& ring, int warp,
+                                                   int nwarps) {
   if (D.vec) {
     if (D.n != 1 || D.log2NC != 2) return false;
-    tile_scatter_vec(D, r0, r1, j0, kbe, acc);
+    tile_scatter_vec<TA>(D, r0, r1, j0, kbe, acc);
     return true;
   }
   if (D.lr) {
@@ -536,10 +540,10 @@ __device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int6
     // boxes would not match what the host encoded.
     if (D.tmap == nullptr || j0 != 0 || kbe != (int32_t)D.k) return false;
     switch (D.log2NC) {
-      case 2: return tile_scatter_lr<4>(D, r0, r1, g, acc, ring, warp, nwarps);
-      case 3: return tile_scatter_lr<8>(D, r0, r1, g, acc, ring, warp, nwarps);
-      case 4: return tile_scatter_lr<16>(D, r0, r1, g, acc, ring, warp, nwarps);
-      case 5: return tile_scatter_lr<32>(D, r0, r1, g, acc, ring, warp, nwarps);
+      case 2: return tile_scatter_lr<4, TA>(D, r0, r1, g, acc, ring, warp, nwarps);
+      case 3: return tile_scatter_lr<8, TA>(D, r0, r1, g, acc, ring, warp, nwarps);
+      case 4: return tile_scatter_lr<16, TA>(D, r0, r1, g, acc, ring, warp, nwarps);
+      case 5: return tile_scatter_lr<32, TA>(D, r0, r1, g, acc, ring, warp, nwarps);
       default: return false;
     }
   }
@@ -550,14 +554,14 @@ __device__ __forceinline__ bool tile_scatter(const TileDesc& D, int64_t r0, int6
   if (D.tmap != nullptr && D.mb > 1 && !(ppr == 1 || ppr == 2 || ppr == 4 || ppr == 8)) return false;
   if (D.tmap != nullptr) {
     switch (ppr) {
-      case 1: return tile_scatter_tma<1>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
-      case 2: return tile_scatter_tma<2>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
-      case 4: return tile_scatter_tma<4>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
-      case 8: return tile_scatter_tma<8>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+      case 1: return tile_scatter_tma<1, TA>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+      case 2: return tile_scatter_tma<2, TA>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+      case 4: return tile_scatter_tma<4, TA>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+      case 8: return tile_scatter_tma<8, TA>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
       default: break;
     }
   }
-  return tile_scatter_t<0>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
+  return tile_scatter_t<0, TA>(D, r0, r1, g, j0, kbe, acc, wbuf, ring, warp, nwarps);
 }
 
 // Scale and (FP16 rules) quantize four consecutive columns of output row r (chunk t): x = fl32(scale

@@ -21,13 +21,14 @@ SK_PARAM_TILE_COLS, SK_PARAM_THREADS, SK_PARAM_LAST_LAUNCHES, SK_PARAM_LAST_CHUN
 SK_PARAM_DEVICE_STATUS, SK_PARAM_LAST_KERNEL, SK_PARAM_SOLVE_GROUP_ROWS = 9, 10, 11
 SK_MODE_ATOMIC, SK_MODE_DETERMINISTIC, SK_MODE_SERIAL_TILE = 0, 1, 2
 SK_KERNEL_AUTO, SK_KERNEL_TILE, SK_KERNEL_LITERAL, SK_KERNEL_OWNER, SK_KERNEL_GLOBAL = 0, 1, 2, 3, 4
+SK_A_FP32, SK_A_FP16, SK_A_BF16 = 0, 1, 2
 
 # Every symbol include/sk.h declares.
 EXPORTS = [
     "sk_version", "sk_last_error", "sk_plan_create", "sk_plan_set", "sk_plan_get", "sk_apply",
     "sk_apply_host", "sk_solve", "sk_solve_status", "sk_solve_precond", "sk_materialize_S", "sk_batch_create",
     "sk_batch_set", "sk_batch_launch", "sk_batch_info", "sk_batch_destroy", "sk_destroy",
-    "sk_apply_noalloc",
+    "sk_apply_noalloc", "sk_apply_typed",
 ]
 
 
@@ -94,6 +95,8 @@ def load(path: str | None = None):
     L.sk_destroy.argtypes = [vp]
     L.sk_apply_noalloc.restype = st
     L.sk_apply_noalloc.argtypes = [vp, vp, i64, i64, vp, vp]
+    L.sk_apply_typed.restype = st
+    L.sk_apply_typed.argtypes = [vp, vp, i32, i64, i64, vp, vp]
     _lib = L
     return L
 
@@ -147,6 +150,10 @@ def sk_plan_get(plan: int, key: int) -> int:
 
 def sk_apply(plan: int, A, lda: int, n: int, Y, stream=None) -> None:
     check(load().sk_apply(plan, _ptr(A), lda, n, _ptr(Y), _stream_handle(stream)))
+
+
+def sk_apply_typed(plan: int, A, a_type: int, lda: int, n: int, Y, stream=None) -> None:
+    check(load().sk_apply_typed(plan, _ptr(A), a_type, lda, n, _ptr(Y), _stream_handle(stream)))
 
 
 def sk_apply_host(plan: int, A_host_ptr: int, lda: int, n: int, Y_host_ptr: int, stream=None) -> None:
@@ -250,13 +257,18 @@ class Plan:
         return torch.bfloat16 if self.rule == SK_BF16_RN else torch.float16
 
     def apply(self, A, Y=None, stream=None):
+        """Y = S A for a CUDA matrix A of float32, float16 or bfloat16 (16-bit A: sk_apply_typed)."""
         import torch
-        if A.dtype != torch.float32 or not A.is_cuda or A.dim() != 2 or A.stride(1) != 1:
-            raise ValueError("A must be a CUDA float32 matrix with unit column stride")
+        a_types = {torch.float32: SK_A_FP32, torch.float16: SK_A_FP16, torch.bfloat16: SK_A_BF16}
+        if A.dtype not in a_types or not A.is_cuda or A.dim() != 2 or A.stride(1) != 1:
+            raise ValueError("A must be a CUDA float32, float16 or bfloat16 matrix with unit column stride")
         n = A.shape[1]
         if Y is None:
             Y = torch.empty((self.d, n), dtype=self.out_dtype(), device=A.device)
-        sk_apply(self.handle, A, A.stride(0), n, Y, stream)
+        if A.dtype == torch.float32:
+            sk_apply(self.handle, A, A.stride(0), n, Y, stream)
+        else:
+            sk_apply_typed(self.handle, A, a_types[A.dtype], A.stride(0), n, Y, stream)
         return Y
 
     def solve(self, A, b, x=None, stream=None):
