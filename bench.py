@@ -394,10 +394,7 @@ def bench_paper_ls(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 24), reps=2):
     The least-squares optimum (FP64 QR of [A | b] by torch) is the normal-equations reference.
     On the coherent problem the paper's per-element FP16 scheme (R = 1, literal kernel) also runs."""
     import torch
-    from paper_2606_20195_gb300 import sk
-    torch.backends.cuda.matmul.allow_tf32 = False
-    g = torch.Generator(device=dev)
-    g.manual_seed(5303)
+    from paper_2606_20195_gb300 import inputs, sk
     methods = [("sparsestack", ZETA, r) for r in ("fp32", "fp16_rn", "fp16_sr", "fp16_dither", "bf16_rn")]
     methods += [("countsketch", 1, "fp32"), ("countsketch", 1, "fp16_rn")]
     step = 1 << 18
@@ -419,23 +416,11 @@ def bench_paper_ls(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 24), reps=2):
         return float(abs(R[n, n])) / float(torch.linalg.vector_norm(b.double()))
 
     def problems():
-        U = torch.linalg.qr(torch.randn((m, n), generator=g, device=dev)).Q
-        V = torch.linalg.qr(torch.randn((n, n), generator=g, device=dev)).Q
-        sig = torch.linspace(100.0, 1.0, n, device=dev)
-        A = ((U * sig) @ V.T).contiguous()
-        del U
-        Ae = A.sum(dim=1)
-        yield "dense_easy", A, (Ae + 1e-3 * torch.randn(m, generator=g, device=dev)).contiguous()
-        yield "dense_hard", A, (Ae + 1e-1 * torch.randn(m, generator=g, device=dev) + 1e-1).contiguous()
-        del A, Ae
-        tau = 1e-3
-        G = torch.randn((m - n, n), generator=g, device=dev) * (tau / (m - n) ** 0.5)
-        xs = torch.randn(n, generator=g, device=dev)
-        A = torch.cat([torch.eye(n, device=dev), G])
-        b = torch.cat([xs + 0.5 * torch.randn(n, generator=g, device=dev), G @ xs])
-        del G
-        perm = torch.randperm(m, generator=g, device=dev)
-        yield "coherent_permuted", A[perm].contiguous(), b[perm].contiguous()
+        torch.backends.cuda.matmul.allow_tf32 = False
+        for fam in ("dense_easy", "dense_hard", "coherent_permuted"):
+            A, b = inputs.paper_ls_problem(fam, m, n, seed=5303, device=str(dev))
+            yield fam, A, b
+            del A, b
 
     out = {"workload": f"m={m} n={n}, d/n in {list(ratios)}; SparseStack k={ZETA}, CountSketch k=1", "families": {}}
     for name, A, b in problems():

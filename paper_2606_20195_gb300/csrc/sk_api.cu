@@ -443,10 +443,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, in
   L.status = p->dstatus;
   L.P = nullptr;
   if (cfg.slices > 1 || cfg.glob) {
-    int64_t chunks;
-    int32_t ncg, nbg;
-    tile_geometry(L, &chunks, &ncg, &nbg);
-    const size_t needP = sizeof(float) * (size_t)chunks * (size_t)(p->d * n);
+    const size_t needP = sizeof(float) * (size_t)launch_P_floats(L);
     if (p->tileP_bytes < needP) {
       if (p->tileP) cudaFree(p->tileP);
       p->tileP = nullptr;

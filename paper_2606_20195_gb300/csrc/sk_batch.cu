@@ -225,6 +225,7 @@ sk_status build_batch(sk_batch_s* b) {
     BatchDesc& D = descs[i];
     D.D.A = it.A_dev;
     D.D.a_type = kAF32;
+    D.D.ldy = 0;
     D.D.Y = it.Y_dev;
     D.D.lda = it.lda;
     D.D.n = it.n;

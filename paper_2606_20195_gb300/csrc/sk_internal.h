@@ -23,7 +23,7 @@ struct TileLaunch {
   int32_t threads;  // threads per CTA
   int32_t grid;     // CTAs (0 = automatic)
   int32_t slices;   // work items per chunk (> 1: two-level combine through P)
-  float* P;         // slices > 1: chunks x d x n FP32 scratch, zero on entry, zero on exit
+  float* P;         // chunk totals, launch_P_floats(L) FP32 (slices > 1 or glob); zero on entry and on exit
   unsigned* status;   // sticky device status word (may be null)
   int64_t col_off;    // global column index of column 0 (keys the rounding random bits)
   int32_t allow_tma;  // stage A through TMA when its layout allows it
@@ -57,6 +57,11 @@ int32_t own_ctas_per_sm(int32_t rule, size_t smem);
 cudaError_t launch_own(const TileLaunch& L, cudaStream_t st, int32_t* launches);
 // Chunks, column groups and block groups of a launch.
 void tile_geometry(const TileLaunch& L, int64_t* chunks, int32_t* ncg, int32_t* nbg);
+// Passes of the global-accumulator kernel: column slabs of *ns columns and batches of *cb chunks,
+// chosen so that the chunk totals of one pass (cb x d x ns FP32) stay resident in L2.
+void global_passes(const TileLaunch& L, int64_t* ns, int64_t* cb);
+// FP32 elements of chunk-total scratch P a launch needs (0: none).
+int64_t launch_P_floats(const TileLaunch& L);
 // Resident CTAs per SM of the tile kernel for (rule, threads, dynamic shared memory).
 int32_t tile_ctas_per_sm(int32_t rule, int32_t threads, size_t smem);
 

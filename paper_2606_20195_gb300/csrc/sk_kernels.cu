@@ -159,44 +159,105 @@ __global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P,
   }
 }
 
+// Chunk totals of one pass kept at most this large, so that they stay in L2 (129 MB) while A streams
+// past: beyond it the FP32 reductions into P miss L2 and each total line travels to DRAM and back
+// several times.
+constexpr int64_t kGlobalPassBytes = (int64_t)40 << 20;
+
+// Measured on GB300 (n = 1024, m = 2^21): with k = 4, passes raise the throughput at d/n = 16, 32 and
+// 64 by 28-46 %; slabs narrower than 128 columns leave most lanes of a row's warp idle and repeat the
+// row's hash per slab (d/n = 256: 622 -> 368 GB/s), and at k = 1 (few reductions per row) the extra
+// launches cost more than the L2 misses they avoid. Those cases keep one pass over all chunks.
+void global_passes(const TileLaunch& L, int64_t* ns, int64_t* cb) {
+  const int64_t t_first = L.row_begin / L.R;
+  const int64_t chunks = (L.row_end - 1) / L.R - t_first + 1;
+  const int64_t per_col = L.d * 4;  // bytes of one column of one chunk total
+  *ns = L.n;
+  *cb = chunks;
+  if (chunks * L.n * per_col <= kGlobalPassBytes || L.k < 2) return;
+  const int64_t cb_fit = kGlobalPassBytes / (L.n * per_col);
+  if (cb_fit >= 1) {
+    *cb = cb_fit;
+    return;
+  }
+  // one chunk at a time is still too large: column slabs (multiples of 4 columns), if wide enough
+  const int64_t slab = (kGlobalPassBytes / per_col) & ~(int64_t)3;
+  if (slab < 128) return;
+  *cb = 1;
+  *ns = slab;
+}
+
+int64_t launch_P_floats(const TileLaunch& L) {
+  if (L.glob) {
+    int64_t ns, cb;
+    global_passes(L, &ns, &cb);
+    return cb * L.d * ns;
+  }
+  if (L.slices > 1) {
+    int64_t chunks;
+    int32_t ncg, nbg;
+    tile_geometry(L, &chunks, &ncg, &nbg);
+    return chunks * L.d * L.n;
+  }
+  return 0;
+}
+
+// The global-accumulator kernel in passes (column slabs x chunk batches, ascending chunks within
+// each slab): each pass reduces into P and its chunk finish adds the pass's chunk totals into Y in
+// chunk order and clears P for the next pass.
 cudaError_t launch_global(const TileLaunch& L, cudaStream_t st, int32_t* launches) {
   if (!L.P) return cudaErrorInvalidValue;
-  TileDesc D;
-  memset(&D, 0, sizeof(D));
   const int64_t B = L.d / L.k;
-  D.A = L.A;
-  D.Y = L.Y;
-  D.lda = L.lda;
-  D.n = L.n;
-  D.row_base = L.row_begin;
-  D.seed = L.seed;
-  D.scale = L.scale;
-  D.B = (uint32_t)B;
-  D.k = (uint32_t)L.k;
-  D.kp = (uint32_t)((L.k + 1) / 2);
-  D.log2NC = 2;
-  D.S = 1;
-  D.kb = L.k;
-  D.col_off = L.col_off;
-  D.a_type = L.a_type;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int64_t rows = L.row_end - L.row_begin;
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, (int64_t)sms * 8));
-  const int64_t t_first = L.row_begin / L.R;
-  switch (L.a_type) {
-    case kAF16: global_kernel<__half><<<(unsigned)grid, 256, 0, st>>>(D, L.P, L.row_end, L.R, t_first); break;
-    case kABF16: global_kernel<__nv_bfloat16><<<(unsigned)grid, 256, 0, st>>>(D, L.P, L.row_end, L.R, t_first); break;
-    default: global_kernel<float><<<(unsigned)grid, 256, 0, st>>>(D, L.P, L.row_end, L.R, t_first); break;
+  int64_t ns, cb;
+  global_passes(L, &ns, &cb);
+  const size_t es_a = (L.a_type == kAF32) ? 4 : 2;
+  const size_t es_y = (L.rule == kFP32) ? 4 : 2;
+  const int64_t t_begin = L.row_begin / L.R;
+  const int64_t t_end = (L.row_end - 1) / L.R;
+  for (int64_t c0 = 0; c0 < L.n; c0 += ns) {
+    const int64_t nsl = std::min(ns, L.n - c0);
+    for (int64_t t0 = t_begin; t0 <= t_end; t0 += cb) {
+      const int64_t t1 = std::min(t0 + cb - 1, t_end);
+      const int64_t rb = std::max(L.row_begin, t0 * L.R);
+      const int64_t re = std::min(L.row_end, (t1 + 1) * L.R);
+      TileDesc D;
+      memset(&D, 0, sizeof(D));
+      D.A = static_cast<const char*>(L.A) + es_a * (size_t)((rb - L.row_begin) * L.lda + c0);
+      D.a_type = L.a_type;
+      D.Y = static_cast<char*>(L.Y) + es_y * (size_t)c0;
+      D.ldy = L.n;
+      D.lda = L.lda;
+      D.n = nsl;
+      D.row_base = rb;
+      D.seed = L.seed;
+      D.scale = L.scale;
+      D.B = (uint32_t)B;
+      D.k = (uint32_t)L.k;
+      D.kp = (uint32_t)((L.k + 1) / 2);
+      D.log2NC = 2;
+      D.S = 1;
+      D.kb = L.k;
+      D.col_off = L.col_off + c0;
+      const int64_t rows = re - rb;
+      const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, (int64_t)sms * 8));
+      switch (L.a_type) {
+        case kAF16: global_kernel<__half><<<(unsigned)grid, 256, 0, st>>>(D, L.P, re, L.R, t0); break;
+        case kABF16: global_kernel<__nv_bfloat16><<<(unsigned)grid, 256, 0, st>>>(D, L.P, re, L.R, t0); break;
+        default: global_kernel<float><<<(unsigned)grid, 256, 0, st>>>(D, L.P, re, L.R, t0); break;
+      }
+      if (launches) *launches += 1;
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      e = launch_chunk_finish(D, L.rule, L.P, t0, t1 - t0 + 1, st, launches);
+      if (e != cudaSuccess) return e;
+    }
   }
-  if (launches) *launches += 1;
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int64_t chunks = (L.row_end - 1) / L.R - t_first + 1;
-  return launch_chunk_finish(D, L.rule, L.P, t_first, chunks, st, launches);
+  return cudaSuccess;
 }
 
 cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches) {
@@ -230,6 +291,7 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   P.status = L.status;
   P.D.col_off = L.col_off;
   P.D.a_type = L.a_type;
+  P.D.ldy = 0;
   P.D.tmap = nullptr;
   if (P.slices > 1 && !P.P) return cudaErrorInvalidValue;
   CUtensorMap tmap;

@@ -57,10 +57,7 @@ extern "C" SK_API sk_status sk_apply_noalloc(sk_plan p, const float* A, int64_t 
   void* base = nullptr;
   s = scratch_address(&base);
   if (s != SK_OK) return s;
-  int64_t chunks;
-  int32_t ncg, nbg;
-  tile_geometry(L, &chunks, &ncg, &nbg);
-  const size_t need_P = (L.slices > 1 || L.glob) ? sizeof(float) * (size_t)chunks * (size_t)(L.d * L.n) : 0;
+  const size_t need_P = sizeof(float) * (size_t)launch_P_floats(L);
   if (kStatusBytes + need_P > kScratchBytes)
     return set_error(SK_ERR_UNSUPPORTED,
                      "sk_apply_noalloc: this size needs %zu bytes of scratch, above the %zu-byte static array; "

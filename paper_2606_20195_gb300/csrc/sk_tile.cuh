@@ -45,6 +45,8 @@ struct TileDesc {
   int32_t lr;       // 1: every work item holds all k blocks and takes the lane-row TMA path
   int32_t vec;      // 1: n = 1, one thread per row (tile_scatter_vec)
   int32_t a_type;   // element type of A (AType: FP32, binary16, bfloat16)
+  int64_t ldy;      // row stride of Y in elements (0: n); the chunk finish of a column slab writes
+                    // columns [0, n) of a wider Y
 };
 
 // Launch parameters of the chunked kernels (tile kernel and owner kernel).
@@ -640,7 +642,8 @@ __device__ __forceinline__ void finish_quad(const TileDesc& D, uint32_t r, int64
   const int64_t n = D.n;
   const int ne = (int)min((int64_t)4, n - col0);
   const bool vec = (n & 3) == 0;
-  const int64_t off = (int64_t)r * n + col0;
+  const int64_t off = (int64_t)r * n + col0;                         // in P (d x n per chunk)
+  const int64_t offy = (int64_t)r * (D.ldy > 0 ? D.ldy : n) + col0;  // in Y
   float yf[4] = {0.f, 0.f, 0.f, 0.f};
   uint16_t yh[4] = {0, 0, 0, 0};
   bool loaded = false, touched = false;
@@ -664,10 +667,10 @@ __device__ __forceinline__ void finish_quad(const TileDesc& D, uint32_t r, int64
     if (!loaded) {
       loaded = true;
       if (RULE == kFP32) {
-        const float* y = reinterpret_cast<const float*>(D.Y) + off;
+        const float* y = reinterpret_cast<const float*>(D.Y) + offy;
         for (int e = 0; e < ne; ++e) yf[e] = y[e];
       } else {
-        const uint16_t* y = reinterpret_cast<const uint16_t*>(D.Y) + off;
+        const uint16_t* y = reinterpret_cast<const uint16_t*>(D.Y) + offy;
         for (int e = 0; e < ne; ++e) yh[e] = y[e];
       }
     }
@@ -685,10 +688,10 @@ __device__ __forceinline__ void finish_quad(const TileDesc& D, uint32_t r, int64
   }
   if (!touched) return;
   if (RULE == kFP32) {
-    float* y = reinterpret_cast<float*>(D.Y) + off;
+    float* y = reinterpret_cast<float*>(D.Y) + offy;
     for (int e = 0; e < ne; ++e) y[e] = yf[e];
   } else {
-    uint16_t* y = reinterpret_cast<uint16_t*>(D.Y) + off;
+    uint16_t* y = reinterpret_cast<uint16_t*>(D.Y) + offy;
     for (int e = 0; e < ne; ++e) y[e] = yh[e];
   }
 }

@@ -80,6 +80,40 @@ def ls_problem_host(m: int, n: int, family: str = "coherent", seed: int = 0, noi
     return A, b, x_star
 
 
+def paper_ls_problem(family: str, m: int = 1 << 21, n: int = 1024, seed: int = 5303, device: str = "cuda:0"):
+    """(A, b) of the paper's least-squares families (Sec. 5.3), float32 on the device.
+
+    dense_easy / dense_hard: A = U diag(sigma) V^T, U and V the Q factors of Gaussian matrices,
+    sigma linear from 100 to 1; b = A 1 + noise, with noise 1e-3 N(0,1) (easy) or 1e-1 N(0,1) + 1e-1
+    (hard). coherent_permuted: A = [I_n; tau G / sqrt(m - n)], tau = 1e-3, b = [x* + eta;
+    (tau G / sqrt(m - n)) x*], x* ~ N(0,1), eta ~ 0.5 N(0,1), rows permuted at random."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    if family in ("dense_easy", "dense_hard"):
+        U = torch.linalg.qr(torch.randn((m, n), generator=g, device=device)).Q
+        V = torch.linalg.qr(torch.randn((n, n), generator=g, device=device)).Q
+        sig = torch.linspace(100.0, 1.0, n, device=device)
+        A = ((U * sig) @ V.T).contiguous()
+        del U
+        b = A.sum(dim=1)
+        if family == "dense_easy":
+            b += 1e-3 * torch.randn(m, generator=g, device=device)
+        else:
+            b += 1e-1 * torch.randn(m, generator=g, device=device) + 1e-1
+        return A, b.contiguous()
+    if family == "coherent_permuted":
+        tau = 1e-3
+        G = torch.randn((m - n, n), generator=g, device=device) * (tau / (m - n) ** 0.5)
+        xs = torch.randn(n, generator=g, device=device)
+        A = torch.cat([torch.eye(n, device=device), G])
+        b = torch.cat([xs + 0.5 * torch.randn(n, generator=g, device=device), G @ xs])
+        del G
+        perm = torch.randperm(m, generator=g, device=device)
+        return A[perm].contiguous(), b[perm].contiguous()
+    raise ValueError(f"unknown least-squares family {family!r}")
+
+
 def batch_shapes(count: int = 256, seed: int = 0, log2_lo: float = 12.0, log2_hi: float = 20.0,
                  ns=(8, 16, 32, 64, 128)):
     """(m_i, n_i, family_i) for the batched workload: m log-uniform in [2^lo, 2^hi], n uniform in ns,

@@ -80,3 +80,25 @@ def test_tile_slices_exact_on_integer_data_any_chunking(sk, dev):
         assert kern == sk.SK_KERNEL_TILE
         ref = oracle.sketch_canonical(A, d, k, 3, rule, R)
         assert np.array_equal(got, ref), (rule, np.count_nonzero(got != ref))
+
+
+# Chunk totals too large for L2 (chunks x d x n x 4 bytes above the pass budget of 40 MiB): the
+# global kernel runs in passes of chunk batches and column slabs, each finished into Y in chunk order
+# before the next. Small-integer data keeps every sum exact, so the result must equal the canonical
+# order bit for bit, over slab boundaries (including a ragged last slab) and chunk batches.
+@pytest.mark.parametrize("shape,R,rules", [
+    ((20000, 256, 65536, 2), 0, [0, 1]),        # 64 MiB per chunk: one chunk per pass, slabs of 160 columns
+    ((30000, 100, 16384, 4), 4096, [0, 1, 2]),   # 6.25 MiB per chunk: batches of 6 of the 8 chunks
+    ((12000, 402, 32768, 8), 3000, [0, 1]),      # slabs of 320 and 82 columns (82 = 4*20 + 2: ragged quads)
+])
+def test_global_passes_exact_on_integer_data(sk, dev, shape, R, rules):
+    m, n, d, k = shape
+    A = np.random.default_rng(m + n).integers(-3, 4, size=(m, n)).astype(np.float32)
+    for rule in rules:
+        params = {"kernel": sk.SK_KERNEL_GLOBAL}
+        if R:
+            params["chunk_rows"] = R
+        got, (Rg, kern) = _run(sk, A, d, k, rule, 99, dev, **params)
+        assert kern == sk.SK_KERNEL_GLOBAL
+        ref = oracle.sketch_canonical(A, d, k, 99, rule, Rg)
+        assert np.array_equal(got, ref), (rule, np.count_nonzero(got != ref))
