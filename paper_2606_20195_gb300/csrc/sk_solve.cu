@@ -137,13 +137,25 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
     }
     ss = block_sum(ss, red);
     if (threadIdx.x == 0 && ss != 0.0) atomicAdd(&a.nrm[j], ss);
-    for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x) {
-      double dot = 0.0;
-      for (int64_t rl = 0; rl < nown; ++rl) {
-        if (row0 + rl < j) continue;
-        dot += Wl[rl * ldw + j] * Wl[rl * ldw + c];
+    // x^T W[:, c] for this CTA's rows r >= j: four columns per thread at a time (independent
+    // accumulation chains), rows in the inner loop.
+    const int64_t rl0 = max((int64_t)0, min(nown, j - row0));  // first local row with r >= j
+    for (int64_t cb = j + 1 + threadIdx.x; cb <= n; cb += 4 * (int64_t)blockDim.x) {
+      double dot[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int64_t rl = rl0; rl < nown; ++rl) {
+        const double* wrow = Wl + rl * ldw;
+        const double xv = wrow[j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t c = cb + q * (int64_t)blockDim.x;
+          if (c <= n) dot[q] += xv * wrow[c];
+        }
       }
-      if (dot != 0.0) atomicAdd(&a.wv[j * ldw + c], dot);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t c = cb + q * (int64_t)blockDim.x;
+        if (c <= n && dot[q] != 0.0) atomicAdd(&a.wv[j * ldw + c], dot[q]);
+      }
     }
     if (j >= row0 && j < row0 + nown) {
       const int64_t rl = j - row0;
@@ -162,13 +174,11 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
       for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x)
         wsm[c] = __ldcg(&a.wv[j * ldw + c]) - alpha * __ldcg(&L.R[j * ldw + c]);
       __syncthreads();
-      const int64_t ncols = n - j;  // columns j+1 .. n
-      for (int64_t e = threadIdx.x; e < nown * ncols; e += blockDim.x) {
-        const int64_t rl = e / ncols, c = j + 1 + (e - rl * ncols);
-        const int64_t r = row0 + rl;
-        if (r < j) continue;
-        const double vr = (r == j) ? vj : Wl[rl * ldw + j];
-        Wl[rl * ldw + c] -= tau * vr * wsm[c];
+      // rows r >= j, columns j+1 .. n (column j itself is read, never written, here)
+      for (int64_t rl = rl0; rl < nown; ++rl) {
+        double* wrow = Wl + rl * ldw;
+        const double tv = tau * ((row0 + rl == j) ? vj : wrow[j]);
+        for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x) wrow[c] -= tv * wsm[c];
       }
     }
     // The owner's diagonal becomes alpha (the update above reads column j only below the diagonal).
