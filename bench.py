@@ -267,6 +267,24 @@ def eta_of(SU) -> float:
     return float(max(abs(float(ev[-1]) - 1.0), abs(1.0 - float(ev[0]))))
 
 
+def r_factor_of(A, chunk: int = 1 << 18):
+    """R factor (n x n, FP64, diag > 0) of a tall matrix A = Q R by stacked chunk QRs (torch, on A's
+    device)."""
+    import torch
+    Rs = [torch.linalg.qr(A[i0:i0 + chunk].double(), mode="r").R for i0 in range(0, A.shape[0], chunk)]
+    R = torch.linalg.qr(torch.cat(Rs), mode="r").R
+    sgn = torch.sign(torch.diagonal(R))
+    sgn[sgn == 0] = 1.0
+    return R * sgn[:, None]
+
+
+def eta_general(SA, R_A) -> float:
+    """eta(S, Q) for a full-rank A = Q R_A from its sketch: eta of SA R_A^-1 (paper Sec. 5.1)."""
+    import torch
+    SQ = torch.linalg.solve_triangular(R_A.T, SA.double().T, upper=False).T
+    return eta_of(SQ)
+
+
 def coherence_of(U) -> float:
     """mu(U) = (m/n) max_i ||U_i,:||^2 (paper Sec. 5.2, coherence sweep)."""
     m, n = U.shape
@@ -466,6 +484,69 @@ def bench_paper_ls(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 24), reps=2):
     return out
 
 
+def sketch_f64_reference(plan_h, A, d: int, k: int, chunk: int = 1 << 17):
+    """FP64 S A from the plan's nonzero pattern (sk_materialize_S, pinned bit-exact against the
+    oracle by the tests) and torch index_add in FP64: the reference for the relative error."""
+    import torch
+    from paper_2606_20195_gb300 import sk
+    m, n = A.shape
+    Y = torch.zeros((d, n), dtype=torch.float64, device=A.device)
+    rows = torch.empty(chunk * k, dtype=torch.int32, device=A.device)
+    signs = torch.empty(chunk * k, dtype=torch.int8, device=A.device)
+    scale = 1.0 / float(np.sqrt(k))
+    for i0 in range(0, m, chunk):
+        c = min(chunk, m - i0)
+        sk.sk_materialize_S(plan_h, i0, c, rows, signs)
+        r = rows[:c * k].long()
+        v = A[i0:i0 + c].double().repeat_interleave(k, dim=0) * (signs[:c * k].double() * scale)[:, None]
+        Y.index_add_(0, r, v)
+    return Y
+
+
+def bench_families(dev, m, n, d, k, seed=1234):
+    """The sweep shape on the three input families (iid N(0,1), coherent 1e3 I block over an N(0, 1e-6)
+    tail, adversarial row i = g_i e_(i mod n)): FP16-RN and FP32 GB/s, relative Frobenius error of
+    every rule against the FP64 sketch, and eta of FP16-RN against FP32 (same S)."""
+    import torch
+    from paper_2606_20195_gb300 import inputs, sk
+    out = {}
+    for fam in ("incoherent", "coherent", "adversarial"):
+        A = inputs.device_matrix(m, n, fam, seed=7, device=str(dev))
+        row = {}
+        ys = {}
+        for name, rv in sk.RULES.items():
+            plan = sk.Plan(d, m, k, rv, seed=seed)
+            Y = torch.empty((d, n), dtype=y_dtype(rv), device=dev)
+            plan.apply(A, Y)
+            if name in ("fp32", "fp16_rn"):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(3):
+                    plan.apply(A, Y)
+                e1.record()
+                torch.cuda.synchronize()
+                es = 4 if rv == 0 else 2
+                row[f"GB/s_{name}"] = (m * n * 4 + d * n * es) / (e0.elapsed_time(e1) / 3 * 1e-3) / 1e9
+            if name == "fp32":
+                Y64 = sketch_f64_reference(plan.handle, A, d, k)
+            ys[name] = Y.double()
+            plan.close()
+        nrm = float(torch.linalg.norm(Y64))
+        row["rel_fro_vs_fp64"] = {nm: float(torch.linalg.norm(Yv - Y64)) / nrm for nm, Yv in ys.items()}
+        try:
+            R_A = r_factor_of(A)
+            ef = eta_general(ys["fp32"], R_A)
+            eh = eta_general(ys["fp16_rn"], R_A)
+            row["eta_fp32"], row["eta_fp16_rn"] = ef, eh
+        except RuntimeError:
+            row["eta_fp32"] = row["eta_fp16_rn"] = None  # rank-deficient A (adversarial with few rows)
+        out[fam] = row
+        del A, Y64, ys
+        torch.cuda.empty_cache()
+    return out
+
+
 def bench_batch(dev, rule_name="fp16_rn", count=256, reps=5):
     """256 uneven matrices in one persistent launch, captured in a CUDA graph and replayed."""
     import torch
@@ -610,13 +691,16 @@ def main() -> int:
 
     # e2e through the host-buffer entry point (pinned A in, pinned Y out)
     Y_pin = torch.empty((d, n), dtype=y_dtype(rule)).pin_memory()
-    for _ in range(2):
+    for _ in range(max(3, args.warmup)):
         sk.sk_apply_host(plan.handle, A_pin.data_ptr(), n, n, Y_pin.data_ptr(), stream)
     e2e_steps = max(3, min(args.steps, 10))
     torch.cuda.synchronize()
+    call_s = []
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
+        tc = time.perf_counter()
         sk.sk_apply_host(plan.handle, A_pin.data_ptr(), n, n, Y_pin.data_ptr(), stream)
+        call_s.append(time.perf_counter() - tc)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_launches = plan.get(sk.SK_PARAM_LAST_LAUNCHES)
     te = torch.tensor([e2e_s], device=dev)
@@ -645,6 +729,14 @@ def main() -> int:
                 "traffic": traffic_record(kernel_name, args.workload, args.rule), "peak_source": peak_note,
                 "kernel": f"sk::{kernel_name}<{args.rule}>",
                 "algorithmic_bytes_per_launch": bytes_step}
+    # The second ceiling of this path: signed FP32 updates (m n k per launch, k/4 per byte of A),
+    # executed as shared-memory reductions; reported per SM clock beside the HBM fraction.
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    upd_s = m * n * k / (avg_launch_ms * 1e-3)
+    sm_hz = (clocks.get("sm_mhz") or 0) * 1e6
+    roofline["updates"] = {"per_launch": m * n * k, "per_s": upd_s,
+                           "per_clk_per_sm": upd_s / (sms * sm_hz) if sm_hz else None,
+                           "per_byte_of_A": k / 4.0}
 
     extras = {}
     cpu_baseline = None
@@ -658,7 +750,7 @@ def main() -> int:
             es2 = 4 if rv == 0 else 2
             variants[name] = {"GB/s": (m * n * 4 + d * n * es2) / (statistics.mean(per) * 1e-3) / 1e9,
                               "ms": statistics.mean(per)}
-            etas[name] = Yv.double().cpu().numpy()
+            etas[name] = Yv.double()
             p2.close()
         # 16-bit A (sk_apply_typed): the same rows, half the bytes of A read; GB/s of its own
         # algorithmic bytes (2 bytes per element of A).
@@ -682,9 +774,8 @@ def main() -> int:
             p2.close()
             del A16, Y16
         # Distortion eta(S, Q) of the column space of A (A = Q R_A) for every rule (same S).
-        import oracle
-        R_A = oracle.tall_r_factor(A_h)
-        eta = {nm: oracle.distortion_of(Yv, R_A) for nm, Yv in etas.items()}
+        R_A = r_factor_of(A)
+        eta = {nm: eta_general(Yv, R_A) for nm, Yv in etas.items()}
         extras["variants"] = variants
         extras["distortion"] = {"eta_fp32": eta["fp32"], "eta_fp16_rn": eta["fp16_rn"],
                                 "rel_diff": abs(eta["fp16_rn"] - eta["fp32"]) / eta["fp32"],
@@ -693,6 +784,7 @@ def main() -> int:
                                 "rel_diff_bf16": abs(eta["bf16_rn"] - eta["fp32"]) / eta["fp32"],
                                 "gaussian_reference_sqrt_n_over_d": float(np.sqrt(n / d))}
         extras["fp16_vs_fp32_speedup"] = variants["fp16_rn"]["GB/s"] / variants["fp32"]["GB/s"]
+        extras["families"] = bench_families(dev, m, n, d, k)
         gb, cores, sample = cpu_oracle_rate(m, n, d, k, budget_s=10.0)
         cpu_baseline = {"value": gb, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample}
         want = set(args.extras.split(",")) if args.extras else set()
@@ -723,7 +815,10 @@ def main() -> int:
             "cpu_baseline": cpu_baseline,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": m * n * 4,
                     "d2h_bytes_per_step": d * n * es, "launches_per_step": e2e_launches,
-                    "pinned_h2d_copy_GBps": h2d_gbps},
+                    "pinned_h2d_copy_GBps": h2d_gbps,
+                    "per_call_GBps_min_median_max": [bytes_step / max(call_s) / 1e9,
+                                                     bytes_step / statistics.median(call_s) / 1e9,
+                                                     bytes_step / min(call_s) / 1e9]},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             **extras,

@@ -76,19 +76,6 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block-wide sum; every thread receives the result.
-__device__ double block_sum(double v, double* red) {
-  v = warp_sum(v);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  const int nw = blockDim.x >> 5;
-  for (int w = 0; w < nw; ++w) s += red[w];
-  return s;
-}
-
 struct QRArgs {
   SolveLaunch L;
   int32_t rpc;     // rows per CTA
@@ -105,18 +92,57 @@ __device__ __forceinline__ double load_val(const void* p, int64_t idx) {
   else return (double)reinterpret_cast<const float*>(p)[idx];
 }
 
+// Columns c > j + 1 of this CTA's rows r >= j: apply step j's reflector (W[r][c] -= tv_r w_c, with
+// tv_r = tau v_r staged per row; tv = 0 before the first step) and accumulate the next step's partial
+// sums x^T W[:, c] over rows r >= j + 1 (x_r = W[r][j+1] after the update, 0 on row j). Four columns
+// per thread at a time (independent chains), rows in the inner loop; one atomic per column.
+__device__ __forceinline__ void qr_sweep(double* Wl, int64_t ldw, int64_t n, int64_t j, int64_t rl0, int64_t nown,
+                                         const double* tvs, const double* xns, const double* wsm, bool update,
+                                         double* wv_next) {
+  const int64_t jn = j + 1;
+  for (int64_t cb = jn + 1 + threadIdx.x; cb <= n; cb += 4 * (int64_t)blockDim.x) {
+    double dot[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t rl = rl0; rl < nown; ++rl) {
+      double* wrow = Wl + rl * ldw;
+      const double tv = tvs[rl], xv = xns[rl];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t c = cb + q * (int64_t)blockDim.x;
+        if (c <= n) {
+          double w = wrow[c];
+          if (update) {
+            w -= tv * wsm[c];
+            wrow[c] = w;
+          }
+          dot[q] += xv * w;
+        }
+      }
+    }
+    if (wv_next) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t c = cb + q * (int64_t)blockDim.x;
+        if (c <= n && dot[q] != 0.0) atomicAdd(&wv_next[c], dot[q]);
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
-  extern __shared__ __align__(16) double Wl[];  // rpc x (n+1), row-major
-  __shared__ double red[32];
+  // rpc x (n+1) rows of W (row-major), then tv_r and the next column's x_r for each local row
+  extern __shared__ __align__(16) double Wl[];
   __shared__ double sc[4];
   __shared__ double wsm[kQRMaxCols];  // w_c = v^T W[:, c] of the current column step
   const SolveLaunch& L = a.L;
   const int64_t n = L.n, d = L.d, ldw = n + 1;
   const int b = blockIdx.x;
+  const int lane = threadIdx.x & 31;
   const unsigned nb = gridDim.x;
   const int64_t row0 = (int64_t)b * a.rpc;
   const int64_t nown = max((int64_t)0, min((int64_t)a.rpc, d - row0));
+  double* tvs = Wl + (int64_t)a.rpc * ldw;
+  double* xns = tvs + a.rpc;
   // Load own rows of [SA | Sb] as FP64.
   for (int64_t e = threadIdx.x; e < nown * ldw; e += blockDim.x) {
     const int64_t rl = e / ldw, c = e - rl * ldw;
@@ -124,44 +150,27 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
     Wl[e] = (c < n) ? load_val<T>(L.SA, r * L.lda_sa + c) : load_val<T>(L.Sb, r * L.sb_stride);
   }
   __syncthreads();
-  for (int64_t j = 0; j < n; ++j) {
-    // One grid reduction per column: with x = W[j:, j] and v = x - alpha e_j, both ||x||^2 and
-    // v^T W[:, c] = x^T W[:, c] - alpha W[j][c] follow from the partial sums of x^T x and x^T W[:, c]
-    // over each CTA's rows; the owner of row j also publishes that row.
+  // One grid reduction per column: with x = W[j:, j] and v = x - alpha e_j, both ||x||^2 and
+  // v^T W[:, c] = x^T W[:, c] - alpha W[j][c] follow from the partial sums of x^T x and x^T W[:, c]
+  // over each CTA's rows; the owner of row j publishes that row. Step j's update of the trailing
+  // columns and the partial sums of step j + 1 share one pass over the rows (qr_sweep).
+  {
     double ss = 0.0;
     for (int64_t rl = threadIdx.x; rl < nown; rl += blockDim.x) {
-      if (row0 + rl >= j) {
-        const double v = Wl[rl * ldw + j];
-        ss += v * v;
-      }
+      const double x = Wl[rl * ldw];
+      tvs[rl] = 0.0;
+      xns[rl] = x;
+      ss += x * x;
     }
-    ss = block_sum(ss, red);
-    if (threadIdx.x == 0 && ss != 0.0) atomicAdd(&a.nrm[j], ss);
-    // x^T W[:, c] for this CTA's rows r >= j: four columns per thread at a time (independent
-    // accumulation chains), rows in the inner loop.
-    const int64_t rl0 = max((int64_t)0, min(nown, j - row0));  // first local row with r >= j
-    for (int64_t cb = j + 1 + threadIdx.x; cb <= n; cb += 4 * (int64_t)blockDim.x) {
-      double dot[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int64_t rl = rl0; rl < nown; ++rl) {
-        const double* wrow = Wl + rl * ldw;
-        const double xv = wrow[j];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int64_t c = cb + q * (int64_t)blockDim.x;
-          if (c <= n) dot[q] += xv * wrow[c];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t c = cb + q * (int64_t)blockDim.x;
-        if (c <= n && dot[q] != 0.0) atomicAdd(&a.wv[j * ldw + c], dot[q]);
-      }
-    }
-    if (j >= row0 && j < row0 + nown) {
-      const int64_t rl = j - row0;
-      for (int64_t c = j + threadIdx.x; c <= n; c += blockDim.x) L.R[j * ldw + c] = Wl[rl * ldw + c];
-    }
-    if (!grid_arrive_wait(L.bar, nb * (unsigned)(j + 1), L.status)) return;
+    ss = warp_sum(ss);
+    if (lane == 0 && ss != 0.0) atomicAdd(&a.nrm[0], ss);
+    __syncthreads();
+    qr_sweep(Wl, ldw, n, -1, 0, nown, tvs, xns, wsm, false, a.wv);
+    if (row0 == 0 && nown > 0)
+      for (int64_t c = threadIdx.x; c <= n; c += blockDim.x) L.R[c] = Wl[c];
+  }
+  if (!grid_arrive_wait(L.bar, nb, L.status)) return;
+  for (int64_t j = 0; j < n; ++j) {
     // Reflector (every thread): alpha = -sign(x0) ||x||, v_j = x0 - alpha, tau = 2 / v^T v.
     const double norm2 = __ldcg(&a.nrm[j]);
     const double x0 = __ldcg(&L.R[j * ldw + j]);
@@ -169,21 +178,42 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
     const double vj = x0 - alpha;
     const double vtv = (norm2 - x0 * x0) + vj * vj;
     const double tau = (vtv > 0.0) ? 2.0 / vtv : 0.0;
-    // W[r][c] -= tau v_r w_c with w_c = v^T W[:, c] = x^T W[:, c] - alpha W[j][c] (staged once per CTA).
-    if (tau != 0.0) {
-      for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x)
-        wsm[c] = __ldcg(&a.wv[j * ldw + c]) - alpha * __ldcg(&L.R[j * ldw + c]);
-      __syncthreads();
-      // rows r >= j, columns j+1 .. n (column j itself is read, never written, here)
-      for (int64_t rl = rl0; rl < nown; ++rl) {
-        double* wrow = Wl + rl * ldw;
-        const double tv = tau * ((row0 + rl == j) ? vj : wrow[j]);
-        for (int64_t c = j + 1 + threadIdx.x; c <= n; c += blockDim.x) wrow[c] -= tv * wsm[c];
+    const int64_t jn = j + 1;
+    // w_c = x^T W[:, c] - alpha W[j][c] for c > j, staged once per CTA; the rows' own threads use
+    // the same expression for column j + 1.
+    for (int64_t c = jn + threadIdx.x; c <= n; c += blockDim.x)
+      wsm[c] = __ldcg(&a.wv[j * ldw + c]) - alpha * __ldcg(&L.R[j * ldw + c]);
+    const double w_next = (jn <= n) ? __ldcg(&a.wv[j * ldw + jn]) - alpha * __ldcg(&L.R[j * ldw + jn]) : 0.0;
+    // Per row r >= j: tv_r = tau v_r, column j + 1 updated (the next step's x_r), the row's share
+    // of ||x||^2 for step j + 1; the owner's diagonal becomes alpha.
+    const int64_t rl0 = max((int64_t)0, min(nown, j - row0));  // first local row with r >= j
+    double ss = 0.0;
+    for (int64_t rl = rl0 + threadIdx.x; rl < nown; rl += blockDim.x) {
+      const int64_t r = row0 + rl;
+      double* wrow = Wl + rl * ldw;
+      const double tv = tau * ((r == j) ? vj : wrow[j]);
+      tvs[rl] = tv;
+      double xn = 0.0;
+      if (jn <= n) {
+        xn = wrow[jn] - tv * w_next;
+        wrow[jn] = xn;
       }
+      xns[rl] = (r >= jn) ? xn : 0.0;
+      if (r >= jn) ss += xn * xn;
+      if (r == j) wrow[j] = alpha;
     }
-    // The owner's diagonal becomes alpha (the update above reads column j only below the diagonal).
-    if (threadIdx.x == 0 && j >= row0 && j < row0 + nown) Wl[(j - row0) * ldw + j] = alpha;
+    ss = warp_sum(ss);
+    if (jn < n && lane == 0 && ss != 0.0) atomicAdd(&a.nrm[jn], ss);
     __syncthreads();
+    qr_sweep(Wl, ldw, n, j, rl0, nown, tvs, xns, wsm, tau != 0.0, (jn < n) ? a.wv + jn * ldw : nullptr);
+    if (jn < n) {
+      __syncthreads();
+      if (jn >= row0 && jn < row0 + nown) {
+        const int64_t rl = jn - row0;
+        for (int64_t c = jn + threadIdx.x; c <= n; c += blockDim.x) L.R[jn * ldw + c] = Wl[rl * ldw + c];
+      }
+      if (!grid_arrive_wait(L.bar, nb * (unsigned)(jn + 1), L.status)) return;
+    }
   }
   // Final R rows: each owner rewrites its rows of R (diagonal alpha, updated off-diagonals).
   if (!grid_arrive_wait(L.bar, nb * (unsigned)(n + 1), L.status)) return;
@@ -235,7 +265,7 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
 
 // Dynamic shared memory a QR CTA may use: the opt-in limit less the static arrays and a margin.
 size_t solve_smem_budget(size_t smem_optin) {
-  const size_t fixed = sizeof(double) * (kQRMaxCols + 32 + 4) + 2048;
+  const size_t fixed = sizeof(double) * (kQRMaxCols + 4) + 2048;
   return smem_optin > fixed ? smem_optin - fixed : 0;
 }
 
@@ -243,7 +273,7 @@ size_t solve_smem_budget(size_t smem_optin) {
 
 int64_t solve_rows_cap(int64_t n, int32_t sms, size_t smem_optin) {
   if (n < 1 || n + 1 > kQRMaxCols) return 0;
-  return (int64_t)sms * (int64_t)(solve_smem_budget(smem_optin) / ((size_t)(n + 1) * 8));
+  return (int64_t)sms * (int64_t)(solve_smem_budget(smem_optin) / ((size_t)(n + 3) * 8));
 }
 
 int32_t solve_ctas(int64_t d, int64_t n, int32_t sms, size_t smem_optin) {
@@ -252,7 +282,7 @@ int32_t solve_ctas(int64_t d, int64_t n, int32_t sms, size_t smem_optin) {
   int64_t ncta = std::min<int64_t>(sms, std::max<int64_t>(1, (d + 7) / 8));
   for (; ncta <= sms; ++ncta) {
     const int64_t rpc = (d + ncta - 1) / ncta;
-    if ((size_t)rpc * (size_t)(n + 1) * 8 <= budget) return (int32_t)ncta;
+    if ((size_t)rpc * (size_t)(n + 3) * 8 <= budget) return (int32_t)ncta;
   }
   return 0;
 }
@@ -268,7 +298,7 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launche
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(L.bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  const size_t smem = std::max<size_t>((size_t)a.rpc * (size_t)(L.n + 1) * 8, (size_t)L.n * 8);
+  const size_t smem = std::max<size_t>((size_t)a.rpc * (size_t)(L.n + 3) * 8, (size_t)L.n * 8);
   void* args[] = {(void*)&a};
   const void* kern = L.src_fp64          ? (const void*)qr64_kernel<double>
                      : (L.rule == kFP32) ? (const void*)qr64_kernel<float>
