@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -93,8 +94,7 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int = 0):
         self.proc = None
-        self.path = os.path.join(HERE, "gpurun_out" if os.path.isdir(os.path.join(HERE, "gpurun_out")) else ".",
-                                 f".clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"sk_clocks_{os.getpid()}.csv")
         self.gpu = gpu_index
 
     def __enter__(self):

@@ -136,7 +136,8 @@ def test_canonical_within_arithmetic_error_bound(rule, R):
 
 
 def test_canonical_error_shrinks_with_chunking():
-    # The survey's estimate: FP16 error ~ 2e-4 * sqrt(T + 1) for T contributions per output.
+    # Expected FP16 error ~ 2e-4 * sqrt(T + 1) for T rounded contributions per output (one binary16
+    # rounding of relative size ~2^-12 each, independent signs).
     m, n, d, k = 16384, 16, 256, 4
     A = inputs.host_matrix(m, n, "incoherent", seed=0)
     Y64 = oracle.sketch_f64(A, d, k, 0)
