@@ -276,8 +276,13 @@ sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo
   }
   // Where the tile kernel would need several block groups (the target-word scatter, 5-7x slower
   // than the global kernel at n = 1024 and d >= 16384), or only 4-column items for a wide matrix
-  // (each row's hash evaluated n/4 times), AUTO takes the global-accumulator kernel.
-  if (!serial && p->kernel == SK_KERNEL_AUTO && p->tile_cols == 0 && (kb < p->k || (NC <= 4 && n >= 256))) {
+  // (each row's hash evaluated n/4 times), AUTO takes the global-accumulator kernel. So it does for
+  // wide matrices at k <= 2: there the tile kernel's cost is the per-item overhead (hash and staging
+  // per column group for only k * NC updates per row) while the global kernel's k n / 4 L2
+  // reductions per row are few (measured at n = 256 / 1024, d/n = 2: k = 1 1809 -> 3100 and
+  // 2035 -> 3745 GB/s, k = 2 1559 -> 2504 and 1810 -> 2686 GB/s; at k = 4 the two are within 3 %).
+  if (!serial && p->kernel == SK_KERNEL_AUTO && p->tile_cols == 0 &&
+      (kb < p->k || (NC <= 4 && n >= 256) || (p->k <= 2 && n >= 256))) {
     choose_global(p, cfg);
     return SK_OK;
   }

@@ -102,3 +102,16 @@ def test_global_passes_exact_on_integer_data(sk, dev, shape, R, rules):
         assert kern == sk.SK_KERNEL_GLOBAL
         ref = oracle.sketch_canonical(A, d, k, 99, rule, Rg)
         assert np.array_equal(got, ref), (rule, np.count_nonzero(got != ref))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_auto_takes_global_for_wide_matrices_at_low_k(sk, dev, k):
+    # n >= 256 with k <= 2: AUTO routes to the global kernel (the faster one there); on integer data
+    # the result is canonical for every rule (chunk totals exact, finished in chunk order).
+    m, n, d = 30000, 300, 600
+    A = np.random.default_rng(k).integers(-3, 4, size=(m, n)).astype(np.float32)
+    for rule in RULES:
+        got, (R, kern) = _run(sk, A, d, k, rule, 5, dev)
+        assert kern == sk.SK_KERNEL_GLOBAL
+        ref = oracle.sketch_canonical(A, d, k, 5, rule, R)
+        assert np.array_equal(got, ref), (rule, np.count_nonzero(got != ref))
