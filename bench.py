@@ -39,6 +39,10 @@ WORKLOADS = {
     "small_m16384_n16_d256_k4": (16384, 16, 256, 4),
     # same kernel shape at a quarter of the rows: the ncu capture case (256 MiB of A, > L2)
     "profile_m1M_n64_d4096_k8": (1 << 20, 64, 4096, 8),
+    # CountSketch on a wide matrix (the paper's n = 1024 at d/n = 2; AUTO: global-accumulator kernel)
+    "countsketch_m2M_n1024_d2048_k1": (1 << 21, 1024, 2048, 1),
+    # the same at an eighth of the rows (1 GiB of A): its ncu capture case
+    "profile_m256K_n1024_d2048_k1": (1 << 18, 1024, 2048, 1),
 }
 DEFAULT_WORKLOAD = "sweep_m4M_n64_d4096_k8"
 METRIC = "SA sketch HBM GB/s (% of peak) FP16 vs FP32 at equal distortion; p99 solve ms"
@@ -809,7 +813,8 @@ def main() -> int:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f16" if rule != 0 else "f32",
             "data": "synthetic (seeded iid N(0,1) matrix per rank; paper publishes no number for this workload)",
             "config": {"workload": args.workload, "m": m, "n": n, "d": d, "k": k, "rule": args.rule,
-                       "chunk_rows": R_used, "l2": "inputs larger than L2 (1 GiB A), no flush",
+                       "chunk_rows": R_used, "l2": (f"inputs larger than L2 ({m * n * 4 / 2**30:.2f} GiB of A), no flush" if m * n * 4 > 129e6
+                              else "inputs smaller than L2: a cached-input number, not a headline"),
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "roofline": roofline,
             "cpu_baseline": cpu_baseline,

@@ -82,7 +82,8 @@ typedef enum {
    * work item has exactly the canonical FP32 chunk total. SK_KERNEL_GLOBAL (chunk totals
    * accumulated in device memory with FP32 reductions, one warp per row; any block height). AUTO
    * takes the tile kernel, or the global kernel when a block of S is too tall for the tile
-   * kernel's shared-memory accumulator. */
+   * kernel's shared-memory accumulator, when the tile kernel would need several block groups or
+   * only 4-column items of a matrix with n >= 256, and for n >= 256 at k <= 2. */
   SK_PARAM_KERNEL = 4,
   /* Columns per work item of the tile kernel (4, 8, 16 or 32; 0 = automatic). */
   SK_PARAM_TILE_COLS = 5,

@@ -62,6 +62,8 @@ void tile_geometry(const TileLaunch& L, int64_t* chunks, int32_t* ncg, int32_t* 
 void global_passes(const TileLaunch& L, int64_t* ns, int64_t* cb);
 // FP32 elements of chunk-total scratch P a launch needs (0: none).
 int64_t launch_P_floats(const TileLaunch& L);
+// The global-accumulator kernel and its chunk finish, in passes (sk_global.cu); needs L.P.
+cudaError_t launch_global(const TileLaunch& L, cudaStream_t st, int32_t* launches);
 // Resident CTAs per SM of the tile kernel for (rule, threads, dynamic shared memory).
 int32_t tile_ctas_per_sm(int32_t rule, int32_t threads, size_t smem);
 
