@@ -84,6 +84,14 @@ def lib():
             L.sko_sketch_sampled.argtypes = [P, i64, i64, i64, i64, i32, u64, ctypes.c_int, i64, i64, P, P, P, P]
             L.sko_num_threads.restype = ctypes.c_int
             L.sko_num_threads.argtypes = []
+            L.sko_round_to_half_f32_array.restype = None
+            L.sko_round_to_half_f32_array.argtypes = [P, i64, ctypes.c_int, P]
+            L.sko_half_add_array.restype = None
+            L.sko_half_add_array.argtypes = [P, P, i64, P]
+            L.sko_round_to_bf16_f32_array.restype = None
+            L.sko_round_to_bf16_f32_array.argtypes = [P, i64, P]
+            L.sko_bf16_add_array.restype = None
+            L.sko_bf16_add_array.argtypes = [P, P, i64, P]
             _lib = L
     return _lib
 
@@ -165,6 +173,40 @@ def round_to_bf16(x: float) -> int:
 
 def bf16_add(a: int, b: int) -> int:
     return int(lib().sko_bf16_add(a & 0xFFFF, b & 0xFFFF))
+
+
+def round_to_half_array(x: np.ndarray, mode: int = 0) -> np.ndarray:
+    """binary16 bit patterns of float32 values (element-wise round_to_half)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty(x.shape, dtype=np.uint16)
+    lib().sko_round_to_half_f32_array(_ptr(x), x.size, mode, _ptr(out))
+    return out
+
+
+def half_add_array(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Element-wise binary16 sums (bit patterns in, bit patterns out)."""
+    a = np.ascontiguousarray(a, dtype=np.uint16)
+    b = np.ascontiguousarray(b, dtype=np.uint16)
+    out = np.empty(a.shape, dtype=np.uint16)
+    lib().sko_half_add_array(_ptr(a), _ptr(b), a.size, _ptr(out))
+    return out
+
+
+def round_to_bf16_array(x: np.ndarray) -> np.ndarray:
+    """bfloat16 bit patterns of float32 values (element-wise round_to_bf16)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty(x.shape, dtype=np.uint16)
+    lib().sko_round_to_bf16_f32_array(_ptr(x), x.size, _ptr(out))
+    return out
+
+
+def bf16_add_array(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Element-wise bfloat16 sums (bit patterns in, bit patterns out)."""
+    a = np.ascontiguousarray(a, dtype=np.uint16)
+    b = np.ascontiguousarray(b, dtype=np.uint16)
+    out = np.empty(a.shape, dtype=np.uint16)
+    lib().sko_bf16_add_array(_ptr(a), _ptr(b), a.size, _ptr(out))
+    return out
 
 
 def bf16bits_to_f64(h: np.ndarray) -> np.ndarray:

@@ -247,6 +247,29 @@ SKO_EXPORT uint16_t sko_bf16_add(uint16_t a, uint16_t b) {
   return sko_round_to_bf16(sko_bf16_to_double(a) + sko_bf16_to_double(b));
 }
 
+/* Array forms of the conversions and additions above (element-wise, threads over the elements), for
+ * the exhaustive comparisons of the tests: every binary32 pattern rounded to binary16 (mode as for
+ * sko_round_to_half) or bfloat16, and every pair of 16-bit patterns added. No new arithmetic. */
+SKO_EXPORT void sko_round_to_half_f32_array(const float* x, int64_t n, int mode, uint16_t* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) out[i] = sko_round_to_half((double)x[i], mode);
+}
+
+SKO_EXPORT void sko_half_add_array(const uint16_t* a, const uint16_t* b, int64_t n, uint16_t* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) out[i] = sko_half_add(a[i], b[i]);
+}
+
+SKO_EXPORT void sko_round_to_bf16_f32_array(const float* x, int64_t n, uint16_t* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) out[i] = sko_round_to_bf16((double)x[i]);
+}
+
+SKO_EXPORT void sko_bf16_add_array(const uint16_t* a, const uint16_t* b, int64_t n, uint16_t* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) out[i] = sko_bf16_add(a[i], b[i]);
+}
+
 /* ---------------------------------------------------------------- quantizers (paper Sec. 4.2) */
 enum { SKO_FP32 = 0, SKO_FP16_RN = 1, SKO_FP16_SR = 2, SKO_FP16_DITHER = 3, SKO_BF16_RN = 4 };
 

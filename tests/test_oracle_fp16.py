@@ -157,3 +157,22 @@ def test_dither_noise_amplitude_and_rn_fallback():
         for u in (0.0, 0.999999):
             q = oracle.half_to_double(oracle.quantize(x, u, oracle.FP16_DITHER))
             assert abs(q - rn) <= 2 * abs(x) * 2.0**-10 + 2.0**-24
+
+
+def test_array_forms_equal_scalar_forms():
+    # the array entry points (used by the exhaustive GPU pins) are the scalar functions element-wise
+    rng = np.random.default_rng(11)
+    bits = rng.integers(0, 1 << 32, size=4000, dtype=np.uint64).astype(np.uint32)
+    x = bits.view(np.float32)
+    for mode in (0, 1, 2):
+        arr = oracle.round_to_half_array(x, mode)
+        assert all(int(arr[i]) == oracle.round_to_half(float(x[i]), mode) for i in range(0, 4000, 7))
+    arr = oracle.round_to_bf16_array(x)
+    assert all(int(arr[i]) == oracle.round_to_bf16(float(x[i])) for i in range(0, 4000, 7))
+    a = rng.integers(0, 1 << 16, size=4000).astype(np.uint16)
+    b = rng.integers(0, 1 << 16, size=4000).astype(np.uint16)
+    h = oracle.half_add_array(a, b)
+    g = oracle.bf16_add_array(a, b)
+    for i in range(0, 4000, 7):
+        assert int(h[i]) == oracle.half_add(int(a[i]), int(b[i]))
+        assert int(g[i]) == oracle.bf16_add(int(a[i]), int(b[i]))
