@@ -590,29 +590,28 @@ def bench_batch(dev, rule_name="fp16_rn", count=256, reps=5):
             "tuned": params, "graph": True}
 
 
-def bench_serve(dev, count=60, log2_m=(14, 20), seed=0):
-    """Poisson stream of sketch-and-solve requests: continuous batching vs one at a time."""
+def bench_serve(dev, count=1000, warm=200, log2_m=(14, 20), seed=0):
+    """Poisson stream of sketch-and-solve requests: continuous batching vs one at a time. Each
+    measured run serves `count` requests after a warm-up run of `warm` requests of the same mix."""
     from paper_2606_20195_gb300 import serve
-    base_reqs = serve.make_stream(count, rate_hz=0.0, seed=seed, log2_m=log2_m)
     one = serve.Server(slots=1, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
-    one.run_one_at_a_time(serve.make_stream(count, rate_hz=0.0, seed=seed, log2_m=log2_m))
-    cap = one.run_one_at_a_time(base_reqs)
+    one.run_one_at_a_time(serve.make_stream(warm, rate_hz=0.0, seed=seed + 1, log2_m=log2_m))
+    cap = one.run_one_at_a_time(serve.make_stream(count, rate_hz=0.0, seed=seed, log2_m=log2_m))
     capacity = cap["solves_per_s"]
     one.close()
     out = {"workload": f"Poisson sketch-and-solve requests, m log-uniform [2^{log2_m[0]},2^{log2_m[1]}], "
-                       f"n in 16..256, d=16n, k in {{1,4,8}}, 4 rules, 120 GB budget, 8 slots",
+                       f"n in 16..256, d=16n, k in {{1,4,8}}, 4 rules, 120 GB budget, 8 slots; "
+                       f"{count} requests per run after {warm} warm-up requests",
            "one_at_a_time_back_to_back": cap}
     for frac in (0.5, 0.8, 0.95):
-        reqs = serve.make_stream(count, rate_hz=frac * capacity, seed=seed, log2_m=log2_m)
         srv = serve.Server(slots=8, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
-        # warm-up pass over the same shapes (plan scratch and per-stream allocator pools)
-        srv.run(serve.make_stream(count, rate_hz=frac * capacity, seed=seed, log2_m=log2_m))
-        cb = srv.run(reqs)
+        # warm-up pass over the same mix (plan scratch and per-stream allocator pools)
+        srv.run(serve.make_stream(warm, rate_hz=frac * capacity, seed=seed + 1, log2_m=log2_m))
+        cb = srv.run(serve.make_stream(count, rate_hz=frac * capacity, seed=seed, log2_m=log2_m))
         srv.close()
-        reqs1 = serve.make_stream(count, rate_hz=frac * capacity, seed=seed, log2_m=log2_m)
         s1 = serve.Server(slots=1, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
-        s1.run_one_at_a_time(serve.make_stream(count, rate_hz=0.0, seed=seed, log2_m=log2_m))
-        fifo = s1.run_one_at_a_time(reqs1)
+        s1.run_one_at_a_time(serve.make_stream(warm, rate_hz=0.0, seed=seed + 1, log2_m=log2_m))
+        fifo = s1.run_one_at_a_time(serve.make_stream(count, rate_hz=frac * capacity, seed=seed, log2_m=log2_m))
         s1.close()
         out[f"rate_{int(frac * 100)}pct"] = {"rate_hz": frac * capacity, "continuous": cb, "fifo": fifo}
     return out
