@@ -719,7 +719,7 @@ sk_status sk_materialize_S(sk_plan p, int64_t i0, int64_t cnt, int32_t* rows, in
 
 // Solve scratch layout (bytes, each region 256-byte aligned):
 //   Y_A (d*n elements), Y_b (d elements), part (n + n*(n+1) doubles), R (n*(n+1) doubles),
-//   bcast (n doubles), bar (2 words), status (1 word), kappa (1 double).
+//   bcast (n doubles), bar (grid-barrier counters), status (1 word), kappa (1 double).
 namespace {
 struct SolveLayout {
   size_t ya, yb, part, R, bcast, bar, status, kappa, stack[2], total;
@@ -735,7 +735,7 @@ SolveLayout solve_layout(int64_t d, int64_t n, int32_t rule, int64_t stack_group
   L.part = off; off = al256(off + 8 * (size_t)(n + n * (n + 1)));
   L.R = off; off = al256(off + 8 * (size_t)(n * (n + 1)));
   L.bcast = off; off = al256(off + 8 * (size_t)n);
-  L.bar = off; off = al256(off + 8);
+  L.bar = off; off = al256(off + solve_bar_bytes());
   L.status = off; off = al256(off + 4);
   L.kappa = off; off = al256(off + 8);
   for (int i = 0; i < 2; ++i) {

@@ -108,7 +108,7 @@ struct SolveLaunch {
   double* part;     // scratch: partial sums, (ncta) * (n + 2) doubles
   double* R;        // scratch: n x (n+1) doubles (R and Q^T Sb)
   double* bcast;    // scratch: n doubles
-  unsigned* bar;    // scratch: 2 words, zero on entry
+  unsigned* bar;    // scratch: solve_bar_bytes() of barrier counters, zeroed by the launcher
   unsigned* status; // sticky status word
   double* kappa;    // out: max|R_ii| / min|R_ii|
   float* x;         // out: n floats
@@ -118,6 +118,8 @@ struct SolveLaunch {
 int32_t solve_ctas(int64_t d, int64_t n, int32_t sms, size_t smem_optin);
 // Rows one QR launch can hold in shared memory for n columns (0 if n is unsupported).
 int64_t solve_rows_cap(int64_t n, int32_t sms, size_t smem_optin);
+// Bytes of the grid-barrier counters a QR launch uses.
+size_t solve_bar_bytes();
 cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launches);
 
 // Sketch-and-precondition LSQR (sk_lsqr.cu). Device scalars (FP64) of the recurrence:

@@ -29,8 +29,11 @@ namespace sk {
 
 namespace {
 
-// Columns of W = [SA | Sb] the kernel handles (n + 1 <= kQRMaxCols).
+// Columns of W = [SA | Sb] the kernel handles (n + 1 <= kQRMaxCols), and per thread of a 256-thread
+// CTA in one column step.
 constexpr int kQRMaxCols = 1032;
+constexpr int kQRThreads = 256;
+constexpr int kQRColsPerThread = (kQRMaxCols + kQRThreads - 1) / kQRThreads;
 
 // A grid barrier gives up after about two seconds of waiting (in SM clock cycles at ~2 GHz).
 constexpr long long kBarrierCycles = 4000000000ll;
@@ -41,19 +44,29 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// Grid synchronization for a co-resident (cooperative) grid with a monotonic arrival counter
-// (bar[0], zero at launch and never reset): every CTA's thread 0 adds 1 with release semantics after a
-// CTA barrier, then polls with acquire loads until `target` (= grid size x synchronization number)
-// CTAs have arrived. The CTA's writes before the call are visible to every CTA after it. Returns false
-// if this CTA, or any CTA before it, gave up waiting.
+// Grid synchronization for a co-resident (cooperative) grid with monotonic arrival counters (zero at
+// launch and never reset): every CTA's thread 0 adds 1 with release semantics, after a CTA barrier,
+// to counter b mod kBarCounters (128 bytes apart), then polls them with acquire loads until their sum
+// reaches `target` (= grid size x synchronization number). The CTA's writes before the call are
+// visible to every CTA after it. Returns false if this CTA, or any CTA before it, gave up waiting.
+// One counter: spreading the arrivals over 8 counters was measured slower on GB300 (QR at n = 1024,
+// d = 2048: 12.7 -> 14.6 ms), the polls of 8 counters costing more than the queued arrivals.
+constexpr int kBarCounters = 1;
+constexpr int kBarStride = 32;  // unsigned words between counters
+
 __device__ bool grid_arrive_wait(unsigned* bar, unsigned target, unsigned* status) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    unsigned* mine = bar + (blockIdx.x % kBarCounters) * kBarStride;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(mine) : "memory");
     const long long t0 = clock64();
     unsigned polls = 0;
-    while (ld_acquire_u32(bar) < target) {
+    while (true) {
+      unsigned sum = 0;
+#pragma unroll
+      for (int q = 0; q < kBarCounters; ++q) sum += ld_acquire_u32(bar + q * kBarStride);
+      if (sum >= target) break;
       if ((++polls & 255u) == 0) {
         if (clock64() - t0 > kBarrierCycles) {
           atomicOr(status, kStatusTimeout);
@@ -129,7 +142,7 @@ __device__ __forceinline__ void qr_sweep(double* Wl, int64_t ldw, int64_t n, int
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
+__global__ void __launch_bounds__(kQRThreads) qr64_kernel(const QRArgs a) {
   // rpc x (n+1) rows of W (row-major), then tv_r and the next column's x_r for each local row
   extern __shared__ __align__(16) double Wl[];
   __shared__ double sc[4];
@@ -171,19 +184,40 @@ __global__ void __launch_bounds__(256) qr64_kernel(const QRArgs a) {
   }
   if (!grid_arrive_wait(L.bar, nb, L.status)) return;
   for (int64_t j = 0; j < n; ++j) {
-    // Reflector (every thread): alpha = -sign(x0) ||x||, v_j = x0 - alpha, tau = 2 / v^T v.
-    const double norm2 = __ldcg(&a.nrm[j]);
-    const double x0 = __ldcg(&L.R[j * ldw + j]);
-    const double alpha = -copysign(sqrt(norm2), x0);
-    const double vj = x0 - alpha;
-    const double vtv = (norm2 - x0 * x0) + vj * vj;
-    const double tau = (vtv > 0.0) ? 2.0 / vtv : 0.0;
     const int64_t jn = j + 1;
-    // w_c = x^T W[:, c] - alpha W[j][c] for c > j, staged once per CTA; the rows' own threads use
-    // the same expression for column j + 1.
-    for (int64_t c = jn + threadIdx.x; c <= n; c += blockDim.x)
-      wsm[c] = __ldcg(&a.wv[j * ldw + c]) - alpha * __ldcg(&L.R[j * ldw + c]);
-    const double w_next = (jn <= n) ? __ldcg(&a.wv[j * ldw + jn]) - alpha * __ldcg(&L.R[j * ldw + jn]) : 0.0;
+    // Inputs of w_c = x^T W[:, c] - alpha W[j][c] for this thread's columns c > j, loaded while
+    // thread 0 forms the reflector (kQRColsPerThread columns per thread at 256 threads).
+    double wraw[kQRColsPerThread], rraw[kQRColsPerThread];
+#pragma unroll
+    for (int q = 0; q < kQRColsPerThread; ++q) {
+      const int64_t c = jn + threadIdx.x + q * (int64_t)blockDim.x;
+      wraw[q] = (c <= n) ? __ldcg(&a.wv[j * ldw + c]) : 0.0;
+      rraw[q] = (c <= n) ? __ldcg(&L.R[j * ldw + c]) : 0.0;
+    }
+    const double wn_raw = (jn <= n) ? __ldcg(&a.wv[j * ldw + jn]) : 0.0;
+    const double rn_raw = (jn <= n) ? __ldcg(&L.R[j * ldw + jn]) : 0.0;
+    // Reflector, formed once per CTA (FP64 square root and division are long instruction sequences
+    // on this part's FP64 pipe): alpha = -sign(x0) ||x||, v_j = x0 - alpha, tau = 2 / v^T v.
+    if (threadIdx.x == 0) {
+      const double norm2 = __ldcg(&a.nrm[j]);
+      const double x0 = __ldcg(&L.R[j * ldw + j]);
+      const double al = -copysign(sqrt(norm2), x0);
+      const double v0 = x0 - al;
+      const double vtv = (norm2 - x0 * x0) + v0 * v0;
+      sc[0] = al;
+      sc[1] = v0;
+      sc[2] = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+    }
+    __syncthreads();
+    const double alpha = sc[0], vj = sc[1], tau = sc[2];
+    // w_c for c > j, staged once per CTA; the rows' own threads use the same expression for
+    // column j + 1.
+#pragma unroll
+    for (int q = 0; q < kQRColsPerThread; ++q) {
+      const int64_t c = jn + threadIdx.x + q * (int64_t)blockDim.x;
+      if (c <= n) wsm[c] = wraw[q] - alpha * rraw[q];
+    }
+    const double w_next = (jn <= n) ? wn_raw - alpha * rn_raw : 0.0;
     // Per row r >= j: tv_r = tau v_r, column j + 1 updated (the next step's x_r), the row's share
     // of ||x||^2 for step j + 1; the owner's diagonal becomes alpha.
     const int64_t rl0 = max((int64_t)0, min(nown, j - row0));  // first local row with r >= j
@@ -271,6 +305,8 @@ size_t solve_smem_budget(size_t smem_optin) {
 
 }  // namespace
 
+size_t solve_bar_bytes() { return sizeof(unsigned) * kBarCounters * kBarStride; }
+
 int64_t solve_rows_cap(int64_t n, int32_t sms, size_t smem_optin) {
   if (n < 1 || n + 1 > kQRMaxCols) return 0;
   return (int64_t)sms * (int64_t)(solve_smem_budget(smem_optin) / ((size_t)(n + 3) * 8));
@@ -296,7 +332,7 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launche
   a.wv = L.part + L.n;
   cudaError_t e = cudaMemsetAsync(L.part, 0, sizeof(double) * (size_t)(L.n + L.n * (L.n + 1)), st);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(L.bar, 0, 2 * sizeof(unsigned), st);
+  e = cudaMemsetAsync(L.bar, 0, solve_bar_bytes(), st);
   if (e != cudaSuccess) return e;
   const size_t smem = std::max<size_t>((size_t)a.rpc * (size_t)(L.n + 3) * 8, (size_t)L.n * 8);
   void* args[] = {(void*)&a};
@@ -306,7 +342,7 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st, int32_t* launche
                                          : (const void*)qr64_kernel<__half>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)L.ncta), dim3(256), args, smem, st);
+  e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)L.ncta), dim3(kQRThreads), args, smem, st);
   if (launches) *launches += 1;
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -82,3 +82,19 @@ def test_solve_rejects_n_above_1024(sk, dev):
         plan.solve(A, b)
     assert e.value.status == sk.SK_ERR_UNSUPPORTED
     plan.close()
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_solve_n256_serving_shape(sk, dev, rule):
+    # The largest request of the serving mix (n = 256, d = 16 n = 4096): one QR launch.
+    import torch
+    m, n, d, k, seed = 1 << 16, 256, 4096, 4, 13
+    A_h, b_h, _ = inputs.ls_problem_host(m, n, "incoherent", seed=29, noise=0.1)
+    A = torch.from_numpy(A_h).to(dev)
+    b = torch.from_numpy(b_h).to(dev)
+    x, st, kap, _, R = _solve(sk, A, b, d, k, rule, seed, 0)
+    assert st == sk.SK_OK
+    x_or, SAb = _oracle_solve(A_h, b_h, d, k, seed, rule, R)
+    assert np.max(np.abs(x - x_or)) <= 1e-6 * np.max(np.abs(x_or))
+    s = np.linalg.svd(SAb[:, :n], compute_uv=False)
+    assert 1.0 <= kap <= 1.01 * s[0] / s[-1]
