@@ -49,3 +49,17 @@ def test_plan_validation_runs_without_gpu():
         sk.sk_plan_set(h, sk.SK_PARAM_SOLVE_GROUP_ROWS, -1)
     assert e.value.status == sk.SK_ERR_INVALID_ARG
     sk.sk_destroy(h)
+
+
+def test_binding_constants_match_header():
+    # every named constant of include/sk.h (status codes, rules, parameter keys, modes, kernels,
+    # element types) has the same value in the Python binding
+    from paper_2606_20195_gb300 import sk
+    with open(os.path.join(ROOT, "include", "sk.h")) as f:
+        src = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    consts = dict((name, int(val)) for name, val in re.findall(r"\b(SK_[A-Z0-9_]+)\s*=\s*(\d+)", src))
+    assert len(consts) >= 30
+    missing = [c for c in consts if not hasattr(sk, c)]
+    assert not missing, missing
+    wrong = {c: (v, getattr(sk, c)) for c, v in consts.items() if getattr(sk, c) != v}
+    assert not wrong, wrong
