@@ -39,6 +39,8 @@ WORKLOADS = {
     "small_m16384_n16_d256_k4": (16384, 16, 256, 4),
     # same kernel shape at a quarter of the rows: the ncu capture case (256 MiB of A, > L2)
     "profile_m1M_n64_d4096_k8": (1 << 20, 64, 4096, 8),
+    # CountSketch at the sweep shape (k = 1: the tile kernel, one block per row)
+    "countsketch_m4M_n64_d4096_k1": (1 << 22, 64, 4096, 1),
     # CountSketch on a wide matrix (the paper's n = 1024 at d/n = 2; AUTO: global-accumulator kernel)
     "countsketch_m2M_n1024_d2048_k1": (1 << 21, 1024, 2048, 1),
     # the same at an eighth of the rows (1 GiB of A): its ncu capture case

@@ -379,17 +379,17 @@ __device__ __forceinline__ void red_shared_f32(uint32_t addr, float v) {
 }
 
 // One hash round of the lane-row path for lane (r, hp): its row's values at
-// `arow` (NC floats of the staged box), the lane's two blocks at accumulator byte addresses base[e]
-// (target row and column still to add). PRED = false is the straight-line form for rounds in which
-// every lane holds a row and both its blocks exist.
+// `arow` (NC floats of the staged box), the lane's E blocks (2, or 1 when k = 1) at accumulator byte
+// addresses base[e] (target row and column still to add). PRED = false is the straight-line form for
+// rounds in which every lane holds a row and all its blocks exist.
 // `z` is the SplitMix64 state of the lane's stream output (seed + index * golden gamma).
-template <int NC, bool PRED, typename TA>
+template <int NC, bool PRED, typename TA, int E = 2>
 __device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int rot, int flip, const TA* arow,
                                          const uint32_t base[2], const bool bv[2], uint32_t LW) {
   const uint64_t h = splitmix_finalize(z);
   uint32_t ad[2], sg[2];
 #pragma unroll
-  for (int e = 0; e < 2; ++e) {
+  for (int e = 0; e < E; ++e) {
     const uint32_t w = (e ^ flip) ? (uint32_t)h : (uint32_t)(h >> 32);
     ad[e] = base[e] + 4u * word_to_slot(w, D.B) * LW;
     sg[e] = w << 31;
@@ -400,7 +400,7 @@ __device__ __forceinline__ void lr_round(const TileDesc& D, uint64_t z, int rot,
     const uint32_t col = (uint32_t)(c + rot) & (uint32_t)(NC - 1);
     const uint32_t a = __float_as_uint(a_to_f32(arow[col]));
     if (!PRED || bv[0]) red_shared_f32(ad[0] + 4u * col, __uint_as_float(a ^ sg[0]));
-    if (!PRED || bv[1]) red_shared_f32(ad[1] + 4u * col, __uint_as_float(a ^ sg[1]));
+    if (E > 1 && (!PRED || bv[1])) red_shared_f32(ad[1] + 4u * col, __uint_as_float(a ^ sg[1]));
   }
 }
 
@@ -428,7 +428,10 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
   const int SB = RB * D.mb;
   const int r = lane / kp;
   const int hp = lane - r * kp;
-  const int flip = ((2 * hp) / S + r / NC) & 1;
+  // k = 1 (CountSketch): one block per lane, no flip, so that the valid block is e = 0 on every lane
+  // and the round has a single, warp-uniform update per column.
+  const bool single = (D.k == 1);
+  const int flip = single ? 0 : (((2 * hp) / S + r / NC) & 1);
   const int rot = r + RB * (hp / S);
   const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
   uint32_t base[2];
@@ -439,8 +442,8 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
     bv[e] = r < RB && j < (int)D.k;
     base[e] = acc_s + 4u * ((uint32_t)(j / S) * B * LW + (uint32_t)((j % S) * NC));
   }
-  // Every lane holds a row of a full round and both its blocks exist (warp-uniform).
-  const bool full_lanes = (RB * kp == 32) && ((D.k & 1u) == 0);
+  // Every lane holds a row of a full round and all its blocks exist (warp-uniform).
+  const bool full_lanes = (RB * kp == 32) && (((D.k & 1u) == 0) || single);
   const int32_t nrows = (int32_t)(r1 - r0);
   const int32_t nbox = (nrows + SB - 1) / SB;
   const int32_t nmine = (nbox > warp) ? (nbox - 1 - warp) / nwarps + 1 : 0;
@@ -480,12 +483,20 @@ __device__ __forceinline__ bool tile_scatter_lr(const TileDesc& D, int64_t r0, i
     uint64_t z = D.seed + idx0 * kSplitMixGamma;
     const uint64_t dz = (uint64_t)(RB * kp) * kSplitMixGamma;
     if (full_lanes && nr_box == SB) {
-      for (int hb = 0; hb < D.mb; ++hb, z += dz)
-        lr_round<NC, false, TA>(D, z, rot, flip, stage + (hb * RB + r) * NC, base, bv, LW);
+      if (single) {
+        for (int hb = 0; hb < D.mb; ++hb, z += dz)
+          lr_round<NC, false, TA, 1>(D, z, rot, flip, stage + (hb * RB + r) * NC, base, bv, LW);
+      } else {
+        for (int hb = 0; hb < D.mb; ++hb, z += dz)
+          lr_round<NC, false, TA, 2>(D, z, rot, flip, stage + (hb * RB + r) * NC, base, bv, LW);
+      }
     } else {
       for (int hb = 0; hb < D.mb; ++hb, z += dz) {
         const int rr = hb * RB + r;  // row of the box
-        if (r < RB && rr < nr_box) lr_round<NC, true, TA>(D, z, rot, flip, stage + rr * NC, base, bv, LW);
+        if (r < RB && rr < nr_box) {
+          if (single) lr_round<NC, true, TA, 1>(D, z, rot, flip, stage + rr * NC, base, bv, LW);
+          else lr_round<NC, true, TA, 2>(D, z, rot, flip, stage + rr * NC, base, bv, LW);
+        }
       }
     }
     __syncwarp();
