@@ -85,55 +85,55 @@ __global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P,
             }
           }
         }
-        continue;
-      }
-      // QB quads per lane are loaded before any of their reductions, so that a warp has QB row
-      // loads in flight (the reductions' memory clobber keeps later loads from moving above them).
-      for (int64_t q0 = 0; q0 < nq; q0 += 32 * QB) {
-        float4 a[QB];
-#pragma unroll
-        for (int b = 0; b < QB; ++b) {
-          const int64_t q = q0 + b * 32 + lane;
-          a[b] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (q >= nq) continue;
-          const int64_t col0 = 4 * q;
-          if (vec) {
-            if constexpr (std::is_same<TA, float>::value) {
-              a[b] = __ldg(reinterpret_cast<const float4*>(arow + col0));
-            } else {
-              const uint2 u = __ldg(reinterpret_cast<const uint2*>(arow + col0));
-              const TA* h = reinterpret_cast<const TA*>(&u);
-              a[b] = make_float4(a_to_f32(h[0]), a_to_f32(h[1]), a_to_f32(h[2]), a_to_f32(h[3]));
-            }
-          } else {
-            a[b].x = ld_a(arow + col0);
-            if (col0 + 1 < n) a[b].y = ld_a(arow + col0 + 1);
-            if (col0 + 2 < n) a[b].z = ld_a(arow + col0 + 2);
-            if (col0 + 3 < n) a[b].w = ld_a(arow + col0 + 3);
-          }
-        }
-        for (int jj = 0; jj < kk; ++jj) {
-          const uint32_t t = __shfl_sync(0xffffffffu, tw, jj);
-          const uint32_t sg = t & 0x80000000u;
-          float* prow = Pt + (int64_t)(t & 0x7FFFFFFFu) * n;
+      } else {
+        // QB quads per lane are loaded before any of their reductions, so that a warp has QB row
+        // loads in flight (the reductions' memory clobber keeps later loads from moving above them).
+        for (int64_t q0 = 0; q0 < nq; q0 += 32 * QB) {
+          float4 a[QB];
 #pragma unroll
           for (int b = 0; b < QB; ++b) {
             const int64_t q = q0 + b * 32 + lane;
-            if (q >= nq) break;
+            a[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q >= nq) continue;
             const int64_t col0 = 4 * q;
-            float* p = prow + col0;
-            const float x = __uint_as_float(__float_as_uint(a[b].x) ^ sg);
-            const float y = __uint_as_float(__float_as_uint(a[b].y) ^ sg);
-            const float z = __uint_as_float(__float_as_uint(a[b].z) ^ sg);
-            const float w4 = __uint_as_float(__float_as_uint(a[b].w) ^ sg);
-            if ((n & 3) == 0) {
-              asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w4)
-                           : "memory");
+            if (vec) {
+              if constexpr (std::is_same<TA, float>::value) {
+                a[b] = __ldg(reinterpret_cast<const float4*>(arow + col0));
+              } else {
+                const uint2 u = __ldg(reinterpret_cast<const uint2*>(arow + col0));
+                const TA* h = reinterpret_cast<const TA*>(&u);
+                a[b] = make_float4(a_to_f32(h[0]), a_to_f32(h[1]), a_to_f32(h[2]), a_to_f32(h[3]));
+              }
             } else {
-              atomicAdd(p, x);
-              if (col0 + 1 < n) atomicAdd(p + 1, y);
-              if (col0 + 2 < n) atomicAdd(p + 2, z);
-              if (col0 + 3 < n) atomicAdd(p + 3, w4);
+              a[b].x = ld_a(arow + col0);
+              if (col0 + 1 < n) a[b].y = ld_a(arow + col0 + 1);
+              if (col0 + 2 < n) a[b].z = ld_a(arow + col0 + 2);
+              if (col0 + 3 < n) a[b].w = ld_a(arow + col0 + 3);
+            }
+          }
+          for (int jj = 0; jj < kk; ++jj) {
+            const uint32_t t = __shfl_sync(0xffffffffu, tw, jj);
+            const uint32_t sg = t & 0x80000000u;
+            float* prow = Pt + (int64_t)(t & 0x7FFFFFFFu) * n;
+#pragma unroll
+            for (int b = 0; b < QB; ++b) {
+              const int64_t q = q0 + b * 32 + lane;
+              if (q >= nq) break;
+              const int64_t col0 = 4 * q;
+              float* p = prow + col0;
+              const float x = __uint_as_float(__float_as_uint(a[b].x) ^ sg);
+              const float y = __uint_as_float(__float_as_uint(a[b].y) ^ sg);
+              const float z = __uint_as_float(__float_as_uint(a[b].z) ^ sg);
+              const float w4 = __uint_as_float(__float_as_uint(a[b].w) ^ sg);
+              if ((n & 3) == 0) {
+                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w4)
+                             : "memory");
+              } else {
+                atomicAdd(p, x);
+                if (col0 + 1 < n) atomicAdd(p + 1, y);
+                if (col0 + 2 < n) atomicAdd(p + 2, z);
+                if (col0 + 3 < n) atomicAdd(p + 3, w4);
+              }
             }
           }
         }
