@@ -266,11 +266,13 @@ SK_API void sk_batch_destroy(sk_batch batch);
  *   - The first call on each device looks up the device address of that array
  *     (cudaGetSymbolAddress) with the device current; make that first call before any stream
  *     capture on the device.
- *   - Sizes whose scratch exceeds 16 MiB (chunks x d x n x 4 bytes when chunks are split across CTAs)
- *     are rejected with SK_ERR_UNSUPPORTED and a message; use sk_apply for those.
+ *   - Sizes whose scratch exceeds 16 MiB (chunks x d x n x 4 bytes when chunks are split across CTAs,
+ *     the chunk totals of one pass for the global kernel) are rejected with SK_ERR_UNSUPPORTED and a
+ *     message; use sk_apply for those.
  *   - Every call on a device shares the one array: calls that overlap on the GPU (different streams,
  *     or different host threads) race and give wrong results. Serialize them on one stream.
- *   - Only SK_MODE_ATOMIC with the tile or owner kernel is supported (SK_ERR_UNSUPPORTED otherwise).
+ *   - Only SK_MODE_ATOMIC is supported, with the kernel AUTO picks or the tile, owner or global kernel
+ *     (SK_ERR_UNSUPPORTED for the deterministic modes and the literal kernel).
  */
 SK_API sk_status sk_apply_noalloc(sk_plan plan, const float* A_dev, int64_t lda, int64_t n, void* Y_dev, void* stream);
 
