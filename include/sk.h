@@ -1,13 +1,15 @@
 /*
  * sk.h — C ABI of the GB300 SparseStack sketching library (libsk.so).
  *
- * The library forms Y = S*A for a tall FP32 matrix A (m x n, m >> n) with a SparseStack sparse
- * oblivious subspace embedding S (d x m): every column of S holds exactly k nonzeros of value
- * +-1/sqrt(k), one in each block of B = d/k consecutive rows; k = 1 is CountSketch
- * (paper Sec. 2.2, Definition of SparseStack; Sec. 4.1 for the block ranges and the scaling).
- * The sum is accumulated in FP32, or stored in binary16 under deterministic round-to-nearest,
- * exact stochastic or dithered rounding (paper Sec. 4.2). S is never stored: the kernels
- * regenerate it from a counter-based hash of (seed, row, block).
+ * The library forms Y = S*A for a tall matrix A (m x n, m >> n; FP32, or binary16 / bfloat16 through
+ * sk_apply_typed) with a SparseStack sparse oblivious subspace embedding S (d x m): every column of S
+ * holds exactly k nonzeros of value +-1/sqrt(k), one in each block of B = d/k consecutive rows;
+ * k = 1 is CountSketch (paper Sec. 2.2, Definition of SparseStack; Sec. 4.1 for the block ranges and
+ * the scaling). The sum is accumulated in FP32, or stored in binary16 under deterministic
+ * round-to-nearest, exact stochastic or dithered rounding, or in bfloat16 (paper Sec. 4.2). S is never
+ * stored: the kernels regenerate it from a counter-based hash of (seed, row, block). On top of the
+ * sketch: sketch-and-solve and sketch-and-precondition least squares (Sec. 5.1, 5.3) and batched
+ * uneven sketches.
  *
  * Conventions for every entry point
  *   - Pointers named *_dev are CUDA device pointers; *_host are host pointers. The caller owns
