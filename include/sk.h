@@ -82,10 +82,15 @@ typedef enum {
    * multiple of 4, and B*128 bytes of shared memory per block; SK_ERR_UNSUPPORTED otherwise).
    * Inside a work item the owner kernel adds rows in ascending order, so a chunk processed as one
    * work item has exactly the canonical FP32 chunk total. SK_KERNEL_GLOBAL (chunk totals
-   * accumulated in device memory with FP32 reductions, one warp per row; any block height). AUTO
-   * takes the tile kernel, or the global kernel when a block of S is too tall for the tile
-   * kernel's shared-memory accumulator, when the tile kernel would need several block groups or
-   * only 4-column items of a matrix with n >= 256, and for n >= 256 at k <= 2. */
+   * accumulated in device memory with FP32 reductions, one warp per row; any block height).
+   * SK_KERNEL_REGISTER (chunk accumulation in registers: every 8 lanes own 8 output rows x 32
+   * columns, rows of A are routed to their owners through per-row lists in shared memory, no
+   * floating-point atomics on chip; needs FP32 A, 16-byte aligned with lda a multiple of 4, and
+   * atomic mode; SK_ERR_UNSUPPORTED otherwise). AUTO takes the register kernel for FP32 A with
+   * k >= 2, n >= 32 and B = d/k <= 512 (except n >= 256 with k = 2) when A's layout allows TMA
+   * (and neither SK_PARAM_TILE_COLS nor SK_PARAM_THREADS is set); otherwise the tile kernel, or the global kernel when a block of S is
+   * too tall for the tile kernel's shared-memory accumulator, when the tile kernel would need several
+   * block groups or only 4-column items of a matrix with n >= 256, and for n >= 256 at k <= 2. */
   SK_PARAM_KERNEL = 4,
   /* Columns per work item of the tile kernel (4, 8, 16 or 32; 0 = automatic). */
   SK_PARAM_TILE_COLS = 5,
@@ -99,16 +104,29 @@ typedef enum {
    * bounded wait gave up, the results of that call are invalid). Reading it synchronizes the device. */
   SK_PARAM_DEVICE_STATUS = 9,
   /* Read-only: the kernel the last sketch ran: SK_KERNEL_TILE (1), SK_KERNEL_LITERAL (2),
-   * SK_KERNEL_OWNER (3), SK_KERNEL_GLOBAL (4), or 5 for the deterministic-mode kernel; 0 before the
-   * first sketch. */
+   * SK_KERNEL_OWNER (3), SK_KERNEL_GLOBAL (4), 5 for the deterministic-mode kernel, or
+   * SK_KERNEL_REGISTER (6); 0 before the first sketch. */
   SK_PARAM_LAST_KERNEL = 10,
   /* Rows per group of sk_solve's tree QR (0, the default: as many rows as the GPU's shared memory
    * holds, so a sketch that fits is factored by one launch). Values below 2n are raised to 2n. */
-  SK_PARAM_SOLVE_GROUP_ROWS = 11
+  SK_PARAM_SOLVE_GROUP_ROWS = 11,
+  /* Register kernel: list entries per output row and staged box of rows (0, the default: chosen from
+   * the block height so that a list overflows with probability about 1e-3; 1..64 imposes it). Rows
+   * beyond a full list are added into the chunk totals by FP32 vector reductions instead, with the
+   * same result up to FP32 summation order; small values exercise that path. */
+  SK_PARAM_LIST_CAP = 12
 } sk_param;
 
 enum { SK_MODE_ATOMIC = 0, SK_MODE_DETERMINISTIC = 1, SK_MODE_SERIAL_TILE = 2 };
-enum { SK_KERNEL_AUTO = 0, SK_KERNEL_TILE = 1, SK_KERNEL_LITERAL = 2, SK_KERNEL_OWNER = 3, SK_KERNEL_GLOBAL = 4 };
+enum {
+  SK_KERNEL_AUTO = 0,
+  SK_KERNEL_TILE = 1,
+  SK_KERNEL_LITERAL = 2,
+  SK_KERNEL_OWNER = 3,
+  SK_KERNEL_GLOBAL = 4,
+  /* 5 is the deterministic-mode kernel's number in SK_PARAM_LAST_KERNEL; it cannot be requested. */
+  SK_KERNEL_REGISTER = 6
+};
 
 typedef struct sk_plan_s* sk_plan;
 

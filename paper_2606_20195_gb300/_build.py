@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsk.so")
-SOURCES = ["sk_kernels.cu", "sk_kernels_a16.cu", "sk_global.cu", "sk_own.cu", "sk_batch.cu", "sk_solve.cu", "sk_lsqr.cu", "sk_api.cu", "sk_noalloc.cu"]
+SOURCES = ["sk_kernels.cu", "sk_kernels_a16.cu", "sk_global.cu", "sk_own.cu", "sk_reg.cu", "sk_batch.cu", "sk_solve.cu", "sk_lsqr.cu", "sk_api.cu", "sk_noalloc.cu"]
 HEADERS = ["sk_device.cuh", "sk_tile.cuh", "sk_tile_kernel.cuh", "sk_internal.h", "sk_hostutil.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

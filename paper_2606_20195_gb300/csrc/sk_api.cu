@@ -49,6 +49,7 @@ struct sk_plan_s {
   int32_t tile_cols = 0;
   int32_t threads = 0;
   int64_t solve_group_rows = 0;  // rows per QR group of sk_solve (0: as many as shared memory holds)
+  int32_t list_cap = 0;          // register kernel: list entries per output row and box (0: automatic)
   int64_t last_launches = 0, last_R = 0;
   int32_t last_kernel = 0;  // kernel of the last sketch: 1 tile, 2 literal, 3 owner, 4 global, 5 deterministic
   // device scratch
@@ -106,6 +107,8 @@ struct TileCfg {
   bool own = false;
   bool vec = false;
   bool glob = false;
+  bool reg = false;
+  int32_t reg_nsub = 0, reg_cap = 0;
 };
 
 // Default chunk length: at most 8 chunks per matrix (each output then receives at most 8 rounded
@@ -189,8 +192,46 @@ void choose_global(const sk_plan_s* p, TileCfg* cfg) {
   cfg->glob = true;
 }
 
+// Register-kernel configuration (atomic mode, FP32 A staged through TMA): the staged box and list
+// capacity for the plan's block height, the default chunk length and the slice count. AUTO takes it
+// for k >= 2, n >= 32 and blocks of at most 512 rows (not n >= 256 with k = 2, which goes to the
+// global kernel), where it is faster than the tile kernel
+// (measured at 2^22 x 64: d = 4096, k = 8: 1060 vs 818 GB/s; d = 1024, k = 8: 1520 vs 798; at
+// d = 4096 with k = 4 or 2 (B = 1024, 2048) the tile kernel stays ahead: 1416 vs 1357, 1735 vs 1448).
+bool choose_reg(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, bool tma_ok, bool a_fp32,
+                TileCfg* cfg) {
+  if (p->mode != SK_MODE_ATOMIC || !tma_ok || !a_fp32 || rows >= ((int64_t)1 << 31)) return false;
+  if (p->kernel == SK_KERNEL_AUTO) {
+    if (p->tile_cols != 0 || p->threads != 0 || p->k < 2 || n < 32 || p->B > 512) return false;
+    if (n >= 256 && p->k <= 2) return false;  // the global kernel's case (wide rows, few nonzeros)
+  } else if (p->kernel != SK_KERNEL_REGISTER) {
+    return false;
+  }
+  const size_t optin = (size_t)std::min(di.optin, 232448) - 1024;
+  int32_t nsub = 0, cap = 0;
+  if (!reg_choose_box(p->B, optin, p->list_cap, &nsub, &cap)) return false;
+  const int64_t R = p->R > 0 ? p->R : default_chunk_rows(p->m);
+  const int64_t ncg = (n + 31) / 32;
+  const int64_t ntg = (p->d + reg_targets() - 1) / reg_targets();
+  *cfg = TileCfg();
+  cfg->NC = 32;
+  cfg->kb = p->k;
+  cfg->threads = reg_threads();
+  cfg->R = R;
+  cfg->slices = choose_slices(p, rows, R, ncg, ntg, 1, di);
+  cfg->reg = true;
+  cfg->reg_nsub = nsub;
+  cfg->reg_cap = cap;
+  return true;
+}
+
 sk_status choose_tile(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, TileCfg* cfg,
-                      bool tma_ok = false) {
+                      bool tma_ok = false, bool a_fp32 = true) {
+  if (choose_reg(p, n, rows, di, tma_ok, a_fp32, cfg)) return SK_OK;
+  if (p->kernel == SK_KERNEL_REGISTER)
+    return set_error(SK_ERR_UNSUPPORTED,
+                     "register kernel: needs atomic mode, FP32 A, A 16-byte aligned with lda %% 4 == 0 and fewer "
+                     "than 2^31 rows");
   if (p->kernel == SK_KERNEL_GLOBAL) {
     if (p->mode != SK_MODE_ATOMIC) return set_error(SK_ERR_UNSUPPORTED, "the global kernel runs in atomic mode only");
     choose_global(p, cfg);
@@ -406,7 +447,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, in
     return SK_OK;
   }
   TileCfg cfg;
-  s = choose_tile(p, n, rows, di, &cfg, tma_layout_ok(A, lda, a_type == SK_A_FP32 ? 4 : 2));
+  s = choose_tile(p, n, rows, di, &cfg, tma_layout_ok(A, lda, a_type == SK_A_FP32 ? 4 : 2), a_type == SK_A_FP32);
   if (s != SK_OK) return s;
   if (cfg.own && a_type != SK_A_FP32) return set_error(SK_ERR_UNSUPPORTED, "the owner kernel reads FP32 A only");
   if (R_fixed > 0) cfg.R = R_fixed;
@@ -435,6 +476,9 @@ sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, in
   L.own = cfg.own ? 1 : 0;
   L.vec = cfg.vec ? 1 : 0;
   L.glob = cfg.glob ? 1 : 0;
+  L.reg = cfg.reg ? 1 : 0;
+  L.reg_nsub = cfg.reg_nsub;
+  L.reg_cap = cfg.reg_cap;
   L.col_off = col_off;
   L.allow_tma = cfg.vec ? 0 : 1;
   if (!p->dstatus) {
@@ -447,7 +491,7 @@ sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, in
   }
   L.status = p->dstatus;
   L.P = nullptr;
-  if (cfg.slices > 1 || cfg.glob) {
+  if (cfg.slices > 1 || cfg.glob || cfg.reg) {
     const size_t needP = sizeof(float) * (size_t)launch_P_floats(L);
     if (p->tileP_bytes < needP) {
       if (p->tileP) cudaFree(p->tileP);
@@ -464,8 +508,12 @@ sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, in
     L.P = p->tileP;
   }
   cudaError_t e = launch_tile(L, st, launches);
-  if (e != cudaSuccess) return cuda_fail(e, cfg.glob ? "global kernel launch" : cfg.own ? "owner kernel launch" : "tile kernel launch");
-  p->last_kernel = cfg.glob ? SK_KERNEL_GLOBAL : cfg.own ? SK_KERNEL_OWNER : SK_KERNEL_TILE;
+  if (e != cudaSuccess)
+    return cuda_fail(e, cfg.glob  ? "global kernel launch"
+                        : cfg.reg ? "register kernel launch"
+                        : cfg.own ? "owner kernel launch"
+                                  : "tile kernel launch");
+  p->last_kernel = cfg.glob ? SK_KERNEL_GLOBAL : cfg.reg ? SK_KERNEL_REGISTER : cfg.own ? SK_KERNEL_OWNER : SK_KERNEL_TILE;
   if (R_used) *R_used = cfg.R;
   return SK_OK;
 }
@@ -518,7 +566,8 @@ sk_status sk_plan_set(sk_plan p, int32_t key, int64_t v) {
       p->row_offset = v;
       return SK_OK;
     case SK_PARAM_KERNEL:
-      if (v < SK_KERNEL_AUTO || v > SK_KERNEL_GLOBAL) return set_error(SK_ERR_INVALID_ARG, "unknown kernel %lld", (long long)v);
+      if (v < SK_KERNEL_AUTO || (v > SK_KERNEL_GLOBAL && v != SK_KERNEL_REGISTER))
+        return set_error(SK_ERR_INVALID_ARG, "unknown kernel %lld", (long long)v);
       p->kernel = (int32_t)v;
       return SK_OK;
     case SK_PARAM_TILE_COLS:
@@ -534,6 +583,10 @@ sk_status sk_plan_set(sk_plan p, int32_t key, int64_t v) {
     case SK_PARAM_SOLVE_GROUP_ROWS:
       if (v < 0) return set_error(SK_ERR_INVALID_ARG, "solve group rows must be >= 0");
       p->solve_group_rows = v;
+      return SK_OK;
+    case SK_PARAM_LIST_CAP:
+      if (v < 0 || v > 64) return set_error(SK_ERR_INVALID_ARG, "list capacity must be in [0, 64]");
+      p->list_cap = (int32_t)v;
       return SK_OK;
     default:
       return set_error(SK_ERR_INVALID_ARG, "unknown or read-only key %d", key);
@@ -551,6 +604,7 @@ sk_status sk_plan_get(sk_plan p, int32_t key, int64_t* v) {
     case SK_PARAM_TILE_COLS: *v = p->tile_cols; return SK_OK;
     case SK_PARAM_THREADS: *v = p->threads; return SK_OK;
     case SK_PARAM_SOLVE_GROUP_ROWS: *v = p->solve_group_rows; return SK_OK;
+    case SK_PARAM_LIST_CAP: *v = p->list_cap; return SK_OK;
     case SK_PARAM_LAST_LAUNCHES: *v = p->last_launches; return SK_OK;
     case SK_PARAM_LAST_CHUNK_ROWS: *v = p->last_R; return SK_OK;
     case SK_PARAM_LAST_KERNEL: *v = p->last_kernel; return SK_OK;
@@ -1013,6 +1067,9 @@ sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, i
   L->own = cfg.own ? 1 : 0;
   L->vec = cfg.vec ? 1 : 0;
   L->glob = cfg.glob ? 1 : 0;
+  L->reg = cfg.reg ? 1 : 0;
+  L->reg_nsub = cfg.reg_nsub;
+  L->reg_cap = cfg.reg_cap;
   L->col_off = 0;
   L->allow_tma = 1;
   L->status = nullptr;

@@ -176,7 +176,7 @@ int64_t launch_P_floats(const TileLaunch& L) {
     global_passes(L, &ns, &cb);
     return cb * L.d * ns;
   }
-  if (L.slices > 1) {
+  if (L.slices > 1 || L.reg) {
     int64_t chunks;
     int32_t ncg, nbg;
     tile_geometry(L, &chunks, &ncg, &nbg);

@@ -33,6 +33,8 @@ struct TileLaunch {
   int32_t own = 0;    // 1: owner kernel (NC = 32, kb = 1 or 2 blocks per item, A through TMA)
   int32_t vec = 0;    // 1: n = 1 vector path of the tile kernel (NC = 4, no TMA)
   int32_t glob = 0;   // 1: global-accumulator kernel (chunk totals in P, any d); needs P
+  int32_t reg = 0;    // 1: register kernel (FP32 A through TMA, 32 columns x 1024 output rows per item); needs P
+  int32_t reg_nsub = 0, reg_cap = 0;  // register kernel: TMA copies per staged box, list entries per output row
 };
 
 // Shared-memory bytes the tile kernel needs for (B, kb, NC, threads, k, ring depth, rounds per box).
@@ -64,6 +66,15 @@ void global_passes(const TileLaunch& L, int64_t* ns, int64_t* cb);
 int64_t launch_P_floats(const TileLaunch& L);
 // The global-accumulator kernel and its chunk finish, in passes (sk_global.cu); needs L.P.
 cudaError_t launch_global(const TileLaunch& L, cudaStream_t st, int32_t* launches);
+// Register kernel (sk_reg.cu): shared-memory bytes for a box of nsub TMA copies and lists of cap
+// entries; threads per CTA; output rows per work item; the box and capacity for block height B within
+// `smem_limit` bytes (cap_fixed > 0 imposes the capacity; false if nothing fits); and the launch (its
+// chunk finish included; needs L.P).
+size_t reg_smem_bytes(int32_t nsub, int32_t cap);
+int32_t reg_threads();
+int32_t reg_targets();
+bool reg_choose_box(int64_t B, size_t smem_limit, int32_t cap_fixed, int32_t* nsub, int32_t* cap);
+cudaError_t launch_reg(const TileLaunch& L, cudaStream_t st, int32_t* launches);
 // Resident CTAs per SM of the tile kernel for (rule, threads, dynamic shared memory).
 int32_t tile_ctas_per_sm(int32_t rule, int32_t threads, size_t smem);
 

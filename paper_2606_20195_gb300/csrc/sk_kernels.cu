@@ -86,6 +86,7 @@ void tile_geometry(const TileLaunch& L, int64_t* chunks, int32_t* ncg, int32_t* 
 
 cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches) {
   if (L.glob) return launch_global(L, st, launches);
+  if (L.reg) return launch_reg(L, st, launches);
   if (L.own) return launch_own(L, st, launches);
   TileGrid P;
   const int64_t B = L.d / L.k;

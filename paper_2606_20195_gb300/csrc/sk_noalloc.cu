@@ -75,6 +75,7 @@ extern "C" SK_API sk_status sk_apply_noalloc(sk_plan p, const float* A, int64_t 
   int32_t launches = 0;
   e = launch_tile(L, st, &launches);
   if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "sketch kernel launch: %s", cudaGetErrorString(e));
-  noalloc_record(p, launches, L.R, L.glob ? SK_KERNEL_GLOBAL : L.own ? SK_KERNEL_OWNER : SK_KERNEL_TILE);
+  noalloc_record(p, launches, L.R,
+                 L.glob ? SK_KERNEL_GLOBAL : L.reg ? SK_KERNEL_REGISTER : L.own ? SK_KERNEL_OWNER : SK_KERNEL_TILE);
   return SK_OK;
 }

@@ -18,9 +18,10 @@ RULES = {"fp32": SK_FP32, "fp16_rn": SK_FP16_RN, "fp16_sr": SK_FP16_SR, "fp16_di
          "bf16_rn": SK_BF16_RN}
 SK_PARAM_CHUNK_ROWS, SK_PARAM_MODE, SK_PARAM_ROW_OFFSET, SK_PARAM_KERNEL = 1, 2, 3, 4
 SK_PARAM_TILE_COLS, SK_PARAM_THREADS, SK_PARAM_LAST_LAUNCHES, SK_PARAM_LAST_CHUNK_ROWS = 5, 6, 7, 8
-SK_PARAM_DEVICE_STATUS, SK_PARAM_LAST_KERNEL, SK_PARAM_SOLVE_GROUP_ROWS = 9, 10, 11
+SK_PARAM_DEVICE_STATUS, SK_PARAM_LAST_KERNEL, SK_PARAM_SOLVE_GROUP_ROWS, SK_PARAM_LIST_CAP = 9, 10, 11, 12
 SK_MODE_ATOMIC, SK_MODE_DETERMINISTIC, SK_MODE_SERIAL_TILE = 0, 1, 2
 SK_KERNEL_AUTO, SK_KERNEL_TILE, SK_KERNEL_LITERAL, SK_KERNEL_OWNER, SK_KERNEL_GLOBAL = 0, 1, 2, 3, 4
+SK_KERNEL_REGISTER = 6
 SK_A_FP32, SK_A_FP16, SK_A_BF16 = 0, 1, 2
 
 # Every symbol include/sk.h declares.
@@ -240,7 +241,7 @@ class Plan:
         self.handle = sk_plan_create(d, m, k, rule, seed)
         keys = {"chunk_rows": SK_PARAM_CHUNK_ROWS, "mode": SK_PARAM_MODE, "row_offset": SK_PARAM_ROW_OFFSET,
                 "kernel": SK_PARAM_KERNEL, "tile_cols": SK_PARAM_TILE_COLS, "threads": SK_PARAM_THREADS,
-                "solve_group_rows": SK_PARAM_SOLVE_GROUP_ROWS}
+                "solve_group_rows": SK_PARAM_SOLVE_GROUP_ROWS, "list_cap": SK_PARAM_LIST_CAP}
         for name, v in params.items():
             sk_plan_set(self.handle, keys[name], int(v))
 

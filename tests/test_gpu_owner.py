@@ -127,12 +127,12 @@ def test_owner_refuses_unsupported_layouts(sk, dev):
 
 
 def test_auto_owner_and_tile_agree(sk, dev):
-    # On small-integer data (exact arithmetic) AUTO (the tile kernel), the owner kernel and the tile
-    # kernel give the same bits, and the same as the oracle.
+    # On small-integer data (exact arithmetic) AUTO (the register kernel at this shape), the owner
+    # kernel and the tile kernel give the same bits, and the same as the oracle.
     m, n, d, k = 20000, 64, 512, 4
     A = np.random.default_rng(3).integers(-3, 4, size=(m, n)).astype(np.float32)
     auto, R = _run(sk, A, d, k, 1, 11, dev)
-    assert _last_kernel(sk, A, d, k, dev) == sk.SK_KERNEL_TILE
+    assert _last_kernel(sk, A, d, k, dev) == sk.SK_KERNEL_REGISTER
     own, _ = _run(sk, A, d, k, 1, 11, dev, kernel=sk.SK_KERNEL_OWNER)
     tile, _ = _run(sk, A, d, k, 1, 11, dev, kernel=sk.SK_KERNEL_TILE)
     ref = oracle.sketch_canonical(A, d, k, 11, 1, R)
