@@ -19,9 +19,9 @@
  *   - IEEE 754 binary16 rounding (round-to-nearest-even, toward -inf, toward +inf) and binary16
  *     addition, written from the format definition.
  *   - The three quantizers of paper Sec. 4.2: round-to-nearest (default hardware conversion),
- *     exact stochastic rounding (Listing 3 semantics) and dithered rounding (Listing 4
- *     semantics), with the constants the paper leaves open fixed as:
- *     UINT24_TO_FLOAT = 2^-24, ULP_SCALE_FACTOR = 2^-10.
+ *     exact stochastic rounding and dithered rounding, with the two constants the paper leaves
+ *     open fixed as: the scale of the 24-bit random integer that makes the uniform u, 2^-24, and
+ *     the dither amplitude factor (noise = (u - 1/2) * x * factor, about one binary16 ulp), 2^-10.
  *   - The FP64 sketch (dense S times A semantics of Sec. 4.1) and the canonical-order FP32/FP16
  *     accumulation: per output, chunk partials in FP32 over ascending rows, scaled, quantized,
  *     then accumulated in ascending chunk order (FP16 adds are round-to-nearest-even).
@@ -287,23 +287,27 @@ SKO_EXPORT uint16_t sko_quantize(float x, float u, int rule) {
     return sko_round_to_half((double)x, 0);
   }
   if (rule == SKO_FP16_SR) {
-    uint16_t rd = sko_round_to_half((double)x, 1);
-    uint16_t ru = sko_round_to_half((double)x, 2);
-    float frd = (float)sko_half_to_double(rd);
-    float fru = (float)sko_half_to_double(ru);
-    float dist_total = fru - frd;
-    float dist_exact = x - frd;
-    float prod = u * dist_total;
-    return (prod < dist_exact) ? ru : rd;
+    /* Sec. 4.2, exact stochastic rounding: the upper binary16 neighbour with probability
+     * (x - lower) / (upper - lower), decided by comparing u times the gap with the excess of x over
+     * the lower neighbour. Both differences are exact in FP32 (the gap is a power of two; the excess
+     * follows from Sterbenz's lemma); the product u * gap is exact too. */
+    uint16_t lower = sko_round_to_half((double)x, 1);
+    uint16_t upper = sko_round_to_half((double)x, 2);
+    float lo = (float)sko_half_to_double(lower);
+    float gap = (float)sko_half_to_double(upper) - lo;
+    float excess = x - lo;
+    return (u * gap < excess) ? upper : lower;
   }
   if (rule == SKO_BF16_RN) {
     return sko_round_to_bf16((double)x);
   }
   if (rule == SKO_FP16_DITHER) {
-    const float ulp_scale = 1.0f / 1024.0f; /* 2^-10 */
+    /* Sec. 4.2, dithered rounding: zero-mean uniform noise of amplitude x * 2^-10 added in FP32,
+     * then round to nearest even. */
+    const float factor = 1.0f / 1024.0f; /* 2^-10 */
     float centered = u - 0.5f;
-    float amp = x * ulp_scale;
-    float noise = centered * amp;
+    float amplitude = x * factor;
+    float noise = centered * amplitude;
     float y = x + noise;
     return sko_round_to_half((double)y, 0);
   }

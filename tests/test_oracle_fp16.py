@@ -159,6 +159,69 @@ def test_dither_noise_amplitude_and_rn_fallback():
             assert abs(q - rn) <= 2 * abs(x) * 2.0**-10 + 2.0**-24
 
 
+def _dither_switch_index(x, before, after):
+    """Smallest grid index i in [0, 2^24) with dither(x, i / 2^24) != `before` (bisection; the
+    result is monotone in u), after checking the two ends of the grid."""
+    assert oracle.quantize(x, 0.0, oracle.FP16_DITHER) == before
+    assert oracle.quantize(x, (2**24 - 1) / 2**24, oracle.FP16_DITHER) == after
+    lo, hi = 0, 2**24
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if oracle.quantize(x, mid / 2**24, oracle.FP16_DITHER) == before:
+            lo = mid + 1
+        else:
+            hi = mid
+    return lo
+
+
+def test_dither_moves_one_to_its_lower_neighbour_on_a_hand_derived_share_of_u():
+    # Values derived by hand from Sec. 4.2's operation order with factor 2^-10 (not from the code):
+    # for x = 1 and u = i 2^-24, noise = (i - 2^23) 2^-34 is exact, and y = fl32(1 + noise). For
+    # D = 2^23 - i > 0, 1 - D 2^-34 rounds to the FP32 grid of [1/2, 1) (spacing 2^-24) as
+    # 1 - rne(D / 1024) 2^-24. binary16 round-to-nearest sends y to 0x3BFF = 1 - 2^-11 iff
+    # y < 1 - 2^-12 (the midpoint; at the midpoint the tie goes to the even 0x3C00), i.e. iff
+    # rne(D / 1024) > 4096, i.e. D > 4096.5 * 1024 = 2^22 + 512, i.e. i < 2^22 - 512 = 4193792.
+    # Above u = 1/2, y reaches at most fl32(1 + 2^-11 - 2^-34) = 1 + 2^-11, whose tie also goes to
+    # 0x3C00. So the result is 0x3BFF exactly for i < 4193792 and 0x3C00 from there on: dither moves
+    # the exactly representable 1.0 to a neighbour with probability (2^22 - 512) / 2^24.
+    # A factor of 2^-11 would give no move at all (y >= 1 - 2^-12), 2^-9 would reach 0x3BFE, and
+    # rounding the exact 1 + noise without the FP32 step would switch at 2^22.
+    assert _dither_switch_index(1.0, 0x3BFF, 0x3C00) == 4193792
+    assert oracle.quantize(1.0, (4193792 - 1) / 2**24, oracle.FP16_DITHER) == 0x3BFF
+    # x = -1: the noise scales with x, so the same u move -1 towards zero by the same rule.
+    assert _dither_switch_index(-1.0, 0xBBFF, 0xBC00) == 4193792
+    # factor 2^-9 would reach the second neighbour 1 - 2^-10 (0x3BFE) at u = 0; 2^-10 never does
+    assert oracle.quantize(1.0, 0.0, oracle.FP16_DITHER) != 0x3BFE
+
+
+def test_dither_leaves_the_smallest_normal_unmoved():
+    # x = 2^-14 (0x0400): amplitude x 2^-10 = 2^-24, so |noise| <= 2^-25, half the binary16 spacing
+    # 2^-24 on both sides of 2^-14; only u = 0 reaches the midpoint 2^-14 - 2^-25, whose tie goes to the
+    # even 0x0400. Every u gives 0x0400 (below 2^-14 dither is plain round-to-nearest in effect).
+    x = 2.0**-14
+    for i in (0, 1, 2**22, 2**23, 2**24 - 1):
+        assert oracle.quantize(x, i / 2**24, oracle.FP16_DITHER) == 0x0400
+
+
+def test_dither_product_order_is_not_observable():
+    # (u - 1/2) * (x * 2^-10) and ((u - 1/2) * x) * 2^-10 round to the same binary16 value for every
+    # x: multiplying by a power of two is exact outside FP32's subnormal range, and inside it the
+    # noise is below binary16's resolution of any x it is added to. So no test can (or needs to) tell
+    # the two orders apart; here checked on 20000 sampled (x, u) pairs with numpy float32 arithmetic.
+    rng = np.random.default_rng(23)
+    xs = np.concatenate([rng.standard_normal(10000), rng.uniform(-60000, 60000, 5000),
+                         rng.standard_normal(5000) * 1e-6]).astype(np.float32)
+    us = (rng.integers(0, 2**24, size=xs.size) * 2.0**-24).astype(np.float32)
+    f = np.float32(2.0**-10)
+    a = ((us - np.float32(0.5)) * (xs * f)).astype(np.float32)
+    b = (((us - np.float32(0.5)) * xs).astype(np.float32) * f).astype(np.float32)
+    assert np.array_equal(oracle.round_to_half_array((xs + a).astype(np.float32), 0),
+                          oracle.round_to_half_array((xs + b).astype(np.float32), 0))
+    for q in range(0, xs.size, 97):
+        assert oracle.quantize(float(xs[q]), float(us[q]), oracle.FP16_DITHER) == \
+            oracle.round_to_half_array(np.array([xs[q] + a[q]], dtype=np.float32), 0)[0]
+
+
 def test_array_forms_equal_scalar_forms():
     # the array entry points (used by the exhaustive GPU pins) are the scalar functions element-wise
     rng = np.random.default_rng(11)
