@@ -101,7 +101,8 @@ typedef enum {
   /* Read-only: the chunk length R the last sk_apply used. */
   SK_PARAM_LAST_CHUNK_ROWS = 8,
   /* Read-only: sticky status bits the sketch kernels of this plan set on the device (bit 0: a
-   * bounded wait gave up, the results of that call are invalid). Reading it synchronizes the device. */
+   * bounded wait gave up, the results of that call are invalid). Reading it synchronizes the device.
+   * After sk_apply_noalloc it also includes that call's status word (see sk_apply_noalloc). */
   SK_PARAM_DEVICE_STATUS = 9,
   /* Read-only: the kernel the last sketch ran: SK_KERNEL_TILE (1), SK_KERNEL_LITERAL (2),
    * SK_KERNEL_OWNER (3), SK_KERNEL_GLOBAL (4), 5 for the deterministic-mode kernel, or
@@ -114,7 +115,17 @@ typedef enum {
    * the block height so that a list overflows with probability about 1e-3; 1..64 imposes it). Rows
    * beyond a full list are added into the chunk totals by FP32 vector reductions instead, with the
    * same result up to FP32 summation order; small values exercise that path. */
-  SK_PARAM_LIST_CAP = 12
+  SK_PARAM_LIST_CAP = 12,
+  /* Upper bound, in bytes, on the device scratch this plan holds (0, the default: none). A call that
+   * would grow the plan's scratch beyond it returns SK_ERR_OOM before enqueueing any work (Y is left
+   * as it was); for services that admit work under a device-memory budget. */
+  SK_PARAM_SCRATCH_LIMIT = 13,
+  /* Upper bound, in SM clock cycles, on each grid-barrier wait of sk_solve's QR kernel (0, the
+   * default: about two seconds). A barrier that gives up ends the kernel and sk_solve_status returns
+   * SK_ERR_TIMEOUT; small values exist to exercise that path. */
+  SK_PARAM_SOLVE_WAIT_CYCLES = 14,
+  /* Read-only: bytes of device scratch the plan holds now. */
+  SK_PARAM_SCRATCH_BYTES = 15
 } sk_param;
 
 enum { SK_MODE_ATOMIC = 0, SK_MODE_DETERMINISTIC = 1, SK_MODE_SERIAL_TILE = 2 };
@@ -283,9 +294,13 @@ SK_API void sk_batch_destroy(sk_batch batch);
  * lives in one fixed static device array of 16 MiB in this library. The caller still passes A and Y
  * exactly as for sk_apply. The call allocates nothing: no cudaMalloc, cudaFree or allocating library
  * routine; it only enqueues memsets and the kernels on `stream` (the same launches as sk_apply).
- *   - The first call on each device looks up the device address of that array
- *     (cudaGetSymbolAddress) with the device current; make that first call before any stream
- *     capture on the device.
+ *   - Every call looks up the device address of that array (cudaGetSymbolAddress) with the
+ *     calling thread's current device; the first lookup on a device may load the library's device
+ *     code there, so make the first call on each device before any stream capture on it.
+ *   - The kernels' status word lives in the array too: after a call, SK_PARAM_DEVICE_STATUS of the
+ *     plan (which synchronizes the device) reports the status of the most recent no-allocation call
+ *     on the current device (bit 0: a bounded wait gave up and that call's Y is invalid). The word is
+ *     cleared at the start of every call.
  *   - Sizes whose scratch exceeds 16 MiB (chunks x d x n x 4 bytes when chunks are split across CTAs,
  *     the chunk totals of one pass for the global kernel) are rejected with SK_ERR_UNSUPPORTED and a
  *     message; use sk_apply for those.
@@ -295,6 +310,29 @@ SK_API void sk_batch_destroy(sk_batch batch);
  *     (SK_ERR_UNSUPPORTED for the deterministic modes and the literal kernel).
  */
 SK_API sk_status sk_apply_noalloc(sk_plan plan, const float* A_dev, int64_t lda, int64_t n, void* Y_dev, void* stream);
+
+/*
+ * Row-sharded sketches (the one exchange step of a multi-GPU sketch). S depends only on the global row
+ * index, so Y = sum over shards of S[:, rows_g] A[rows_g, :]; summing must happen before the rounding
+ * of the 16-bit rules, on the FP32 chunk totals (the paper's Sec. 4.1 scatter, with the chunked
+ * pre-combine; Sec. 4.2 rounding after the sum). A shard's plan covers its rows: m rows starting at
+ * global row SK_PARAM_ROW_OFFSET, and SK_PARAM_CHUNK_ROWS (R) must be set to the same value on every
+ * shard. P is a device buffer of nchunks x d x n FP32 values, chunk-major (d x n each, row stride n),
+ * 16-byte aligned; slot q holds global chunk t0 + q (the rows [t R, (t+1) R) of chunk t).
+ *
+ * sk_apply_partials — adds into P_dev the FP32 chunk totals of the plan's rows (it does not clear P;
+ *   start from zero). Nothing is rounded. The plan's chunks must lie in [t0, t0 + nchunks).
+ *   Atomic mode only (SK_ERR_UNSUPPORTED otherwise); A_dev, lda, n as for sk_apply.
+ * sk_finish_partials — Y_dev = the sketch from the summed chunk totals: for every output, the chunk
+ *   totals of P_dev in ascending chunk order, each scaled by fl32(1/sqrt(k)), rounded by the plan's rule
+ *   and added into Y (zeroed first), exactly as sk_apply finishes its own chunk totals. Clears P_dev.
+ * With one shard the pair gives sk_apply's result (same chunk totals up to the FP32 summation order
+ * inside a chunk); with several, sum the shards' P (an all-reduce in FP32) between the two calls.
+ */
+SK_API sk_status sk_apply_partials(sk_plan plan, const float* A_dev, int64_t lda, int64_t n, float* P_dev, int64_t t0,
+                                   int64_t nchunks, void* stream);
+SK_API sk_status sk_finish_partials(sk_plan plan, float* P_dev, int64_t t0, int64_t nchunks, int64_t n, void* Y_dev,
+                                    void* stream);
 
 /* Release the plan and its device scratch (synchronizes the device first). NULL is a no-op. */
 SK_API void sk_destroy(sk_plan plan);

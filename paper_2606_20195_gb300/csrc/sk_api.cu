@@ -36,6 +36,10 @@ const char* last_error_message() { return g_err; }
 
 using namespace sk;
 
+namespace sk {
+sk_status noalloc_read_status(unsigned* out);  // sk_noalloc.cu
+}
+
 struct sk_plan_s {
   int64_t d = 0, m = 0, B = 0;
   int32_t k = 0, rule = 0;
@@ -50,8 +54,11 @@ struct sk_plan_s {
   int32_t threads = 0;
   int64_t solve_group_rows = 0;  // rows per QR group of sk_solve (0: as many as shared memory holds)
   int32_t list_cap = 0;          // register kernel: list entries per output row and box (0: automatic)
+  int64_t scratch_limit = 0;     // bound on the plan's device scratch in bytes (0: none)
+  int64_t solve_wait_cycles = 0; // bound on each grid-barrier wait of the QR kernel (0: default)
   int64_t last_launches = 0, last_R = 0;
   int32_t last_kernel = 0;  // kernel of the last sketch: 1 tile, 2 literal, 3 owner, 4 global, 5 deterministic
+  bool last_noalloc = false;  // the last sketch was an sk_apply_noalloc call (status in the static array)
   // device scratch
   float* det_P = nullptr;
   size_t det_P_bytes = 0;
@@ -97,6 +104,31 @@ sk_status dev_info(DevInfo* di) {
 }
 
 size_t elem_size(int32_t rule) { return rule == SK_FP32 ? 4 : 2; }
+
+// Device scratch the plan holds, in bytes.
+size_t plan_scratch_bytes(const sk_plan_s* p) {
+  return p->det_P_bytes + (p->dstatus ? sizeof(unsigned) : 0) + p->tileP_bytes + p->lsqr_bytes + p->solve_bytes +
+         2 * p->stage_bytes + p->ydev_bytes;
+}
+
+// Replace one plan buffer (*ptr of *cur bytes) by a new one of `bytes`: checked against the plan's
+// scratch limit first, so a refused call leaves the plan's buffers as they were and enqueues nothing;
+// SK_ERR_OOM also when cudaMalloc fails.
+template <typename T>
+sk_status plan_grow(sk_plan_s* p, T** ptr, size_t* cur, size_t bytes, const char* what) {
+  if (p->scratch_limit > 0 && plan_scratch_bytes(p) - *cur + bytes > (size_t)p->scratch_limit)
+    return set_error(SK_ERR_OOM, "%s (%zu bytes) would take the plan's scratch above its limit of %lld bytes", what,
+                     bytes, (long long)p->scratch_limit);
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *cur = 0;
+  if (cudaMalloc(reinterpret_cast<void**>(ptr), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(SK_ERR_OOM, "%s (%zu bytes)", what, bytes);
+  }
+  *cur = bytes;
+  return SK_OK;
+}
 
 // Tile-kernel configuration for a plan and a column count.
 struct TileCfg {
@@ -374,10 +406,13 @@ sk_status validate_apply(const sk_plan_s* p, const void* A, int64_t lda, int64_t
 }
 
 // Enqueue Y = S * A for rows [row_begin, row_begin + rows) (A row 0 = row_begin) with chunk rows R.
-// Y must already be zero. a_type: element type of A (SK_A_FP32, SK_A_FP16, SK_A_BF16).
+// Y must already be zero, or zero_y set: then Y is zeroed on the stream once the plan's scratch is in
+// place (a call refused for lack of scratch leaves Y untouched). a_type: element type of A
+// (SK_A_FP32, SK_A_FP16, SK_A_BF16).
 sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, int64_t row_begin, int64_t rows, void* Y,
                          int64_t R_fixed, cudaStream_t st, int32_t* launches, int64_t* R_used, int64_t col_off = 0,
-                         int32_t a_type = SK_A_FP32) {
+                         int32_t a_type = SK_A_FP32, bool zero_y = false) {
+  p->last_noalloc = false;
   DevInfo di;
   sk_status s = dev_info(&di);
   if (s != SK_OK) return s;
@@ -393,14 +428,12 @@ sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, in
     }
     const size_t need = sizeof(float) * (size_t)(p->d * n);
     if (p->det_P_bytes < need) {
-      if (p->det_P) cudaFree(p->det_P);
-      p->det_P = nullptr;
-      p->det_P_bytes = 0;
-      if (cudaMalloc(&p->det_P, need) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(SK_ERR_OOM, "deterministic-mode scratch (%zu bytes)", need);
-      }
-      p->det_P_bytes = need;
+      s = plan_grow(p, &p->det_P, &p->det_P_bytes, need, "deterministic-mode scratch");
+      if (s != SK_OK) return s;
+    }
+    if (zero_y) {
+      cudaError_t ez = cudaMemsetAsync(Y, 0, elem_size(p->rule) * (size_t)(p->d * n), st);
+      if (ez != cudaSuccess) return cuda_fail(ez, "zeroing Y");
     }
     DetLaunch L;
     L.A = A;
@@ -426,6 +459,10 @@ sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, in
   }
   if (literal) {
     if (p->R > 1 || R_fixed > 1) return set_error(SK_ERR_INVALID_ARG, "the literal kernel implements chunk rows R = 1 only");
+    if (zero_y) {
+      cudaError_t ez = cudaMemsetAsync(Y, 0, elem_size(p->rule) * (size_t)(p->d * n), st);
+      if (ez != cudaSuccess) return cuda_fail(ez, "zeroing Y");
+    }
     LiteralLaunch L;
     L.A = A;
     L.a_type = a_type;
@@ -482,10 +519,9 @@ sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, in
   L.col_off = col_off;
   L.allow_tma = cfg.vec ? 0 : 1;
   if (!p->dstatus) {
-    if (cudaMalloc(&p->dstatus, sizeof(unsigned)) != cudaSuccess) {
-      cudaGetLastError();
-      return set_error(SK_ERR_OOM, "status word");
-    }
+    size_t cur = 0;
+    s = plan_grow(p, &p->dstatus, &cur, sizeof(unsigned), "status word");
+    if (s != SK_OK) return s;
     cudaError_t ez = cudaMemsetAsync(p->dstatus, 0, sizeof(unsigned), st);
     if (ez != cudaSuccess) return cuda_fail(ez, "zeroing status word");
   }
@@ -494,18 +530,16 @@ sk_status enqueue_sketch(sk_plan_s* p, const void* A, int64_t lda, int64_t n, in
   if (cfg.slices > 1 || cfg.glob || cfg.reg) {
     const size_t needP = sizeof(float) * (size_t)launch_P_floats(L);
     if (p->tileP_bytes < needP) {
-      if (p->tileP) cudaFree(p->tileP);
-      p->tileP = nullptr;
-      p->tileP_bytes = 0;
-      if (cudaMalloc(&p->tileP, needP) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(SK_ERR_OOM, "chunk-total scratch (%zu bytes)", needP);
-      }
+      s = plan_grow(p, &p->tileP, &p->tileP_bytes, needP, "chunk-total scratch");
+      if (s != SK_OK) return s;
       cudaError_t ez = cudaMemsetAsync(p->tileP, 0, needP, st);
       if (ez != cudaSuccess) return cuda_fail(ez, "zeroing chunk totals");
-      p->tileP_bytes = needP;
     }
     L.P = p->tileP;
+  }
+  if (zero_y) {
+    cudaError_t ez = cudaMemsetAsync(Y, 0, elem_size(p->rule) * (size_t)(p->d * n), st);
+    if (ez != cudaSuccess) return cuda_fail(ez, "zeroing Y");
   }
   cudaError_t e = launch_tile(L, st, launches);
   if (e != cudaSuccess)
@@ -588,6 +622,14 @@ sk_status sk_plan_set(sk_plan p, int32_t key, int64_t v) {
       if (v < 0 || v > 64) return set_error(SK_ERR_INVALID_ARG, "list capacity must be in [0, 64]");
       p->list_cap = (int32_t)v;
       return SK_OK;
+    case SK_PARAM_SCRATCH_LIMIT:
+      if (v < 0) return set_error(SK_ERR_INVALID_ARG, "scratch limit must be >= 0");
+      p->scratch_limit = v;
+      return SK_OK;
+    case SK_PARAM_SOLVE_WAIT_CYCLES:
+      if (v < 0) return set_error(SK_ERR_INVALID_ARG, "solve wait cycles must be >= 0");
+      p->solve_wait_cycles = v;
+      return SK_OK;
     default:
       return set_error(SK_ERR_INVALID_ARG, "unknown or read-only key %d", key);
   }
@@ -605,17 +647,28 @@ sk_status sk_plan_get(sk_plan p, int32_t key, int64_t* v) {
     case SK_PARAM_THREADS: *v = p->threads; return SK_OK;
     case SK_PARAM_SOLVE_GROUP_ROWS: *v = p->solve_group_rows; return SK_OK;
     case SK_PARAM_LIST_CAP: *v = p->list_cap; return SK_OK;
+    case SK_PARAM_SCRATCH_LIMIT: *v = p->scratch_limit; return SK_OK;
+    case SK_PARAM_SOLVE_WAIT_CYCLES: *v = p->solve_wait_cycles; return SK_OK;
+    case SK_PARAM_SCRATCH_BYTES: *v = (int64_t)plan_scratch_bytes(p); return SK_OK;
     case SK_PARAM_LAST_LAUNCHES: *v = p->last_launches; return SK_OK;
     case SK_PARAM_LAST_CHUNK_ROWS: *v = p->last_R; return SK_OK;
     case SK_PARAM_LAST_KERNEL: *v = p->last_kernel; return SK_OK;
     case SK_PARAM_DEVICE_STATUS: {
       *v = 0;
-      if (!p->dstatus) return SK_OK;
+      if (!p->dstatus && !p->last_noalloc) return SK_OK;
       cudaError_t e = cudaDeviceSynchronize();
       if (e != cudaSuccess) return cuda_fail(e, "device status");
       unsigned w = 0;
-      e = cudaMemcpy(&w, p->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) return cuda_fail(e, "device status");
+      if (p->dstatus) {
+        e = cudaMemcpy(&w, p->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "device status");
+      }
+      if (p->last_noalloc) {
+        unsigned wn = 0;
+        sk_status s = noalloc_read_status(&wn);
+        if (s != SK_OK) return s;
+        w |= wn;
+      }
       *v = (int64_t)w;
       return SK_OK;
     }
@@ -629,10 +682,8 @@ sk_status sk_apply(sk_plan p, const float* A, int64_t lda, int64_t n, void* Y, v
   if (s != SK_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   int32_t launches = 0;
-  cudaError_t e = cudaMemsetAsync(Y, 0, elem_size(p->rule) * (size_t)(p->d * n), st);
-  if (e != cudaSuccess) return cuda_fail(e, "zeroing Y");
   int64_t R_used = 0;
-  s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, Y, 0, st, &launches, &R_used);
+  s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, Y, 0, st, &launches, &R_used, 0, SK_A_FP32, true);
   p->last_launches = launches;
   p->last_R = R_used;
   return s;
@@ -646,10 +697,8 @@ sk_status sk_apply_typed(sk_plan p, const void* A, int32_t a_type, int64_t lda, 
   if (s != SK_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   int32_t launches = 0;
-  cudaError_t e = cudaMemsetAsync(Y, 0, elem_size(p->rule) * (size_t)(p->d * n), st);
-  if (e != cudaSuccess) return cuda_fail(e, "zeroing Y");
   int64_t R_used = 0;
-  s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, Y, 0, st, &launches, &R_used, 0, a_type);
+  s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, Y, 0, st, &launches, &R_used, 0, a_type, true);
   p->last_launches = launches;
   p->last_R = R_used;
   return s;
@@ -687,6 +736,10 @@ sk_status sk_apply_host(sk_plan p, const float* A_host, int64_t lda, int64_t n, 
   const size_t tile_bytes = (size_t)tile_rows * (size_t)row_bytes;
   const size_t ybytes = elem_size(p->rule) * (size_t)(p->d * n);
   if (p->stage_bytes < tile_bytes) {
+    // both staging tiles at once against the limit (plan_grow counts stage_bytes twice)
+    if (p->scratch_limit > 0 && plan_scratch_bytes(p) - 2 * p->stage_bytes + 2 * tile_bytes > (size_t)p->scratch_limit)
+      return set_error(SK_ERR_OOM, "host pipeline staging (2 x %zu bytes) would take the plan's scratch above its limit",
+                       tile_bytes);
     for (int b = 0; b < 2; ++b) {
       if (p->stage[b]) cudaFree(p->stage[b]);
       p->stage[b] = nullptr;
@@ -701,14 +754,8 @@ sk_status sk_apply_host(sk_plan p, const float* A_host, int64_t lda, int64_t n, 
     p->stage_bytes = tile_bytes;
   }
   if (p->ydev_bytes < ybytes) {
-    if (p->ydev) cudaFree(p->ydev);
-    p->ydev = nullptr;
-    p->ydev_bytes = 0;
-    if (cudaMalloc(&p->ydev, ybytes) != cudaSuccess) {
-      cudaGetLastError();
-      return set_error(SK_ERR_OOM, "host pipeline Y buffer (%zu bytes)", ybytes);
-    }
-    p->ydev_bytes = ybytes;
+    s = plan_grow(p, &p->ydev, &p->ydev_bytes, ybytes, "host pipeline Y buffer");
+    if (s != SK_OK) return s;
   }
   if (!p->copy_stream) {
     if (cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -829,15 +876,9 @@ sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const floa
   const int64_t groups1 = (p->d > cap) ? (p->d + cap - 1) / cap : 0;
   const SolveLayout Lo = solve_layout(p->d, n, p->rule, groups1);
   if (p->solve_bytes < Lo.total) {
-    if (p->solve_buf) cudaFree(p->solve_buf);
-    p->solve_buf = nullptr;
-    p->solve_bytes = 0;
-    if (cudaMalloc(&p->solve_buf, Lo.total) != cudaSuccess) {
-      cudaGetLastError();
-      return set_error(SK_ERR_OOM, "sketch-and-solve scratch (%zu bytes)", Lo.total);
-    }
+    s = plan_grow(p, &p->solve_buf, &p->solve_bytes, Lo.total, "sketch-and-solve scratch");
+    if (s != SK_OK) return s;
     cudaMemset(p->solve_buf, 0, Lo.total);
-    p->solve_bytes = Lo.total;
   }
   p->solve_status_off = Lo.status;
   p->solve_kappa_off = Lo.kappa;
@@ -857,6 +898,7 @@ sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const floa
   s = enqueue_sketch(p, b, 1, 1, p->row_offset, p->m, base + Lo.yb, R_used, st, &launches, nullptr, n);
   if (s != SK_OK) return s;
   SolveLaunch L;
+  L.wait_cycles = p->solve_wait_cycles;
   L.SA = base + Lo.ya;
   L.Sb = base + Lo.yb;
   L.lda_sa = n;
@@ -924,14 +966,8 @@ sk_status sk_solve_precond(sk_plan p, const float* A, int64_t lda, int64_t n, co
   const size_t nv = (size_t)((n + 31) / 32 * 32);
   const size_t need = sizeof(double) * ((size_t)m + 6 * nv + kLsqrScalars) + sizeof(float) * nv;
   if (p->lsqr_bytes < need) {
-    if (p->lsqr) cudaFree(p->lsqr);
-    p->lsqr = nullptr;
-    p->lsqr_bytes = 0;
-    if (cudaMalloc(&p->lsqr, need) != cudaSuccess) {
-      cudaGetLastError();
-      return set_error(SK_ERR_OOM, "sketch-and-precondition scratch (%zu bytes)", need);
-    }
-    p->lsqr_bytes = need;
+    sk_status sg = plan_grow(p, &p->lsqr, &p->lsqr_bytes, need, "sketch-and-precondition scratch");
+    if (sg != SK_OK) return sg;
   }
   double* base = p->lsqr;
   float* x0f = reinterpret_cast<float*>(base + m + 6 * nv + kLsqrScalars);
@@ -986,6 +1022,116 @@ sk_status sk_solve_precond(sk_plan p, const float* A, int64_t lda, int64_t n, co
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "LSQR result");
   if (iters_out) *iters_out = (int32_t)sc[kLsqrIters];
+  p->last_launches = launches;
+  return SK_OK;
+}
+
+sk_status sk_apply_partials(sk_plan p, const float* A, int64_t lda, int64_t n, float* P, int64_t t0, int64_t nchunks,
+                            void* stream) {
+  clear_error();
+  sk_status s = validate_apply(p, A, lda, n, P);
+  if (s != SK_OK) return s;
+  if ((reinterpret_cast<uintptr_t>(P) & 15u) != 0) return set_error(SK_ERR_INVALID_ARG, "P must be 16-byte aligned");
+  if (p->mode != SK_MODE_ATOMIC || p->kernel == SK_KERNEL_LITERAL)
+    return set_error(SK_ERR_UNSUPPORTED, "sk_apply_partials runs in atomic mode with a chunked kernel");
+  const int64_t R = p->R;
+  if (R <= 0)
+    return set_error(SK_ERR_INVALID_ARG,
+                     "sk_apply_partials needs SK_PARAM_CHUNK_ROWS set (the same on every shard of the matrix)");
+  const int64_t tf = p->row_offset / R, tl = (p->row_offset + p->m - 1) / R;
+  if (t0 < 0 || nchunks < 1 || tf < t0 || tl >= t0 + nchunks)
+    return set_error(SK_ERR_INVALID_ARG, "the plan's chunks [%lld, %lld] are not inside P's chunks [%lld, %lld)",
+                     (long long)tf, (long long)tl, (long long)t0, (long long)(t0 + nchunks));
+  DevInfo di;
+  s = dev_info(&di);
+  if (s != SK_OK) return s;
+  TileCfg cfg;
+  s = choose_tile(p, n, p->m, di, &cfg, tma_layout_ok(A, lda), true);
+  if (s != SK_OK) return s;
+  if (cfg.glob) {
+    // The global kernel finishes its passes as it goes; partials take the tile kernel instead.
+    sk_plan_s tmp = *p;
+    tmp.kernel = SK_KERNEL_TILE;
+    s = choose_tile(&tmp, n, p->m, di, &cfg, tma_layout_ok(A, lda), true);
+    if (s != SK_OK) return s;
+  }
+  cfg.R = R;
+  if (!cfg.reg && cfg.slices < 2) cfg.slices = 2;  // work items flush into the chunk totals
+  if (!p->dstatus) {
+    size_t cur = 0;
+    s = plan_grow(p, &p->dstatus, &cur, sizeof(unsigned), "status word");
+    if (s != SK_OK) return s;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(p->dstatus, 0, sizeof(unsigned), st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "zeroing status");
+  TileLaunch L;
+  L.A = A;
+  L.a_type = SK_A_FP32;
+  L.Y = nullptr;
+  L.lda = lda;
+  L.n = n;
+  L.row_begin = p->row_offset;
+  L.row_end = p->row_offset + p->m;
+  L.d = p->d;
+  L.k = p->k;
+  L.rule = p->rule;
+  L.seed = p->seed;
+  L.scale = p->scale;
+  L.R = R;
+  L.NC = cfg.NC;
+  L.kb = cfg.kb;
+  L.threads = cfg.threads;
+  L.grid = cfg.grid;
+  L.slices = cfg.slices;
+  L.depth = cfg.depth;
+  L.mb = cfg.mb;
+  L.lr = cfg.lr ? 1 : 0;
+  L.own = cfg.own ? 1 : 0;
+  L.vec = cfg.vec ? 1 : 0;
+  L.glob = 0;
+  L.reg = cfg.reg ? 1 : 0;
+  L.reg_nsub = cfg.reg_nsub;
+  L.reg_cap = cfg.reg_cap;
+  L.col_off = 0;
+  L.allow_tma = cfg.vec ? 0 : 1;
+  L.status = p->dstatus;
+  L.P = P + (tf - t0) * p->d * n;
+  L.no_finish = 1;
+  int32_t launches = 0;
+  cudaError_t e = launch_tile(L, st, &launches);
+  if (e != cudaSuccess) return cuda_fail(e, "sketch kernel launch (partials)");
+  p->last_noalloc = false;
+  p->last_launches = launches;
+  p->last_R = R;
+  p->last_kernel = cfg.reg ? SK_KERNEL_REGISTER : cfg.own ? SK_KERNEL_OWNER : SK_KERNEL_TILE;
+  return SK_OK;
+}
+
+sk_status sk_finish_partials(sk_plan p, float* P, int64_t t0, int64_t nchunks, int64_t n, void* Y, void* stream) {
+  clear_error();
+  if (!p) return set_error(SK_ERR_INVALID_ARG, "plan is NULL");
+  if (!P || !Y) return set_error(SK_ERR_INVALID_ARG, "P and Y must not be NULL");
+  if (n < 1 || n > kMaxN) return set_error(SK_ERR_INVALID_ARG, "n=%lld outside [1, %lld]", (long long)n, (long long)kMaxN);
+  if (t0 < 0 || nchunks < 1) return set_error(SK_ERR_INVALID_ARG, "need t0 >= 0 and nchunks >= 1");
+  if ((reinterpret_cast<uintptr_t>(P) & 15u) != 0) return set_error(SK_ERR_INVALID_ARG, "P must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(Y) & 3u) != 0) return set_error(SK_ERR_INVALID_ARG, "Y must be 4-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(Y, 0, elem_size(p->rule) * (size_t)(p->d * n), st);
+  if (e != cudaSuccess) return cuda_fail(e, "zeroing Y");
+  TileDesc D;
+  memset(&D, 0, sizeof(D));
+  D.Y = Y;
+  D.n = n;
+  D.seed = p->seed;
+  D.scale = p->scale;
+  D.B = (uint32_t)p->B;
+  D.k = (uint32_t)p->k;
+  D.kp = (uint32_t)((p->k + 1) / 2);
+  D.col_off = 0;
+  D.ldy = 0;
+  int32_t launches = 0;
+  e = launch_chunk_finish(D, p->rule, P, t0, nchunks, st, &launches);
+  if (e != cudaSuccess) return cuda_fail(e, "chunk-finish launch");
   p->last_launches = launches;
   return SK_OK;
 }
@@ -1083,6 +1229,7 @@ void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R, int32_t kernel) {
   p->last_launches = launches;
   p->last_R = R;
   p->last_kernel = kernel;
+  p->last_noalloc = true;
 }
 
 }  // namespace sk

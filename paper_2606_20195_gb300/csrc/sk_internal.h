@@ -35,6 +35,7 @@ struct TileLaunch {
   int32_t glob = 0;   // 1: global-accumulator kernel (chunk totals in P, any d); needs P
   int32_t reg = 0;    // 1: register kernel (FP32 A through TMA, 32 columns x 1024 output rows per item); needs P
   int32_t reg_nsub = 0, reg_cap = 0;  // register kernel: TMA copies per staged box, list entries per output row
+  int32_t no_finish = 0;  // 1: leave the chunk totals in P (no chunk-finish launch); P is then the caller's
 };
 
 // Shared-memory bytes the tile kernel needs for (B, kb, NC, threads, k, ring depth, rounds per box).
@@ -124,6 +125,7 @@ struct SolveLaunch {
   double* kappa;    // out: max|R_ii| / min|R_ii|
   float* x;         // out: n floats
   int32_t ncta;
+  long long wait_cycles = 0;  // bound on each grid-barrier wait in SM clock cycles (0: about two seconds)
 };
 // CTAs and rows per CTA the QR kernel will use for (d, n); 0 CTAs if unsupported.
 int32_t solve_ctas(int64_t d, int64_t n, int32_t sms, size_t smem_optin);

@@ -154,7 +154,7 @@ cudaError_t launch_tile(const TileLaunch& L, cudaStream_t st, int32_t* launches)
   if (launches) *launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (P.slices > 1) return launch_chunk_finish(P.D, L.rule, P.P, P.t_first, chunks, st, launches);
+  if (P.slices > 1 && !L.no_finish) return launch_chunk_finish(P.D, L.rule, P.P, P.t_first, chunks, st, launches);
   return cudaSuccess;
 }
 

@@ -3,8 +3,6 @@
 // applications that own all device memory). Contract and limits: include/sk.h.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/sk.h"
 #include "sk_hostutil.h"
 #include "sk_internal.h"
@@ -13,6 +11,7 @@ namespace sk {
 sk_status noalloc_tile_launch(const sk_plan_s* p, const float* A, int64_t lda, int64_t n, void* Y, TileLaunch* L);
 size_t noalloc_elem_size(const sk_plan_s* p);
 void noalloc_record(sk_plan_s* p, int64_t launches, int64_t R, int32_t kernel);
+sk_status noalloc_read_status(unsigned* out);
 }  // namespace sk
 
 using namespace sk;
@@ -24,25 +23,15 @@ constexpr size_t kScratchBytes = (size_t)16 << 20;
 constexpr size_t kStatusBytes = 256;  // status word, padded
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device. Looked up on every call (cheap), so a
+// module that the driver loaded again at another address (after cudaDeviceReset, for example) is
+// never addressed through a stale pointer.
 sk_status scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return set_error(SK_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr)
-      return set_error(SK_ERR_CUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
-    g_scratch_addr[dev] = ptr;
-  }
-  *out = g_scratch_addr[dev];
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr)
+    return set_error(SK_ERR_CUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+  *out = ptr;
   return SK_OK;
 }
 
@@ -77,5 +66,14 @@ extern "C" SK_API sk_status sk_apply_noalloc(sk_plan p, const float* A, int64_t 
   if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "sketch kernel launch: %s", cudaGetErrorString(e));
   noalloc_record(p, launches, L.R,
                  L.glob ? SK_KERNEL_GLOBAL : L.reg ? SK_KERNEL_REGISTER : L.own ? SK_KERNEL_OWNER : SK_KERNEL_TILE);
+  return SK_OK;
+}
+
+// The status word of the last no-allocation call on the current device (the first word of the
+// static array; the caller synchronizes first). A symbol copy: allocates nothing.
+sk_status sk::noalloc_read_status(unsigned* out) {
+  *out = 0u;
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_noalloc_scratch, sizeof(unsigned), 0, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_error(SK_ERR_CUDA, "reading the no-allocation status word: %s", cudaGetErrorString(e));
   return SK_OK;
 }

@@ -378,6 +378,7 @@ cudaError_t launch_reg(const TileLaunch& L, cudaStream_t st, int32_t* launches) 
   if (launches) *launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (L.no_finish) return cudaSuccess;
   return launch_chunk_finish(G.D, L.rule, G.P, G.t_first, chunks, st, launches);
 }
 

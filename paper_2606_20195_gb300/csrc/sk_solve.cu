@@ -48,13 +48,14 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // launch and never reset): every CTA's thread 0 adds 1 with release semantics, after a CTA barrier,
 // to counter b mod kBarCounters (128 bytes apart), then polls them with acquire loads until their sum
 // reaches `target` (= grid size x synchronization number). The CTA's writes before the call are
-// visible to every CTA after it. Returns false if this CTA, or any CTA before it, gave up waiting.
+// visible to every CTA after it. Gives up after `limit` SM clock cycles. Returns false if this CTA, or
+// any CTA before it, gave up waiting.
 // One counter: spreading the arrivals over 8 counters was measured slower on GB300 (QR at n = 1024,
 // d = 2048: 12.7 -> 14.6 ms), the polls of 8 counters costing more than the queued arrivals.
 constexpr int kBarCounters = 1;
 constexpr int kBarStride = 32;  // unsigned words between counters
 
-__device__ bool grid_arrive_wait(unsigned* bar, unsigned target, unsigned* status) {
+__device__ bool grid_arrive_wait(unsigned* bar, unsigned target, unsigned* status, long long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -67,8 +68,10 @@ __device__ bool grid_arrive_wait(unsigned* bar, unsigned target, unsigned* statu
 #pragma unroll
       for (int q = 0; q < kBarCounters; ++q) sum += ld_acquire_u32(bar + q * kBarStride);
       if (sum >= target) break;
-      if ((++polls & 255u) == 0) {
-        if (clock64() - t0 > kBarrierCycles) {
+      // the clock is read on the first poll (so that a limit of a few cycles takes effect at once)
+      // and every 256 polls after it
+      if ((++polls & 255u) == 1u || (polls & 255u) == 0u) {
+        if (clock64() - t0 > limit) {
           atomicOr(status, kStatusTimeout);
           break;
         }
@@ -143,6 +146,7 @@ __device__ __forceinline__ void qr_sweep(double* Wl, int64_t ldw, int64_t n, int
 
 template <typename T>
 __global__ void __launch_bounds__(kQRThreads) qr64_kernel(const QRArgs a) {
+  const long long wait = a.L.wait_cycles > 0 ? a.L.wait_cycles : kBarrierCycles;
   // rpc x (n+1) rows of W (row-major), then tv_r and the next column's x_r for each local row
   extern __shared__ __align__(16) double Wl[];
   __shared__ double sc[4];
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(kQRThreads) qr64_kernel(const QRArgs a) {
     if (row0 == 0 && nown > 0)
       for (int64_t c = threadIdx.x; c <= n; c += blockDim.x) L.R[c] = Wl[c];
   }
-  if (!grid_arrive_wait(L.bar, nb, L.status)) return;
+  if (!grid_arrive_wait(L.bar, nb, L.status, wait)) return;
   for (int64_t j = 0; j < n; ++j) {
     const int64_t jn = j + 1;
     // Inputs of w_c = x^T W[:, c] - alpha W[j][c] for this thread's columns c > j, loaded while
@@ -246,11 +250,11 @@ __global__ void __launch_bounds__(kQRThreads) qr64_kernel(const QRArgs a) {
         const int64_t rl = jn - row0;
         for (int64_t c = jn + threadIdx.x; c <= n; c += blockDim.x) L.R[jn * ldw + c] = Wl[rl * ldw + c];
       }
-      if (!grid_arrive_wait(L.bar, nb * (unsigned)(jn + 1), L.status)) return;
+      if (!grid_arrive_wait(L.bar, nb * (unsigned)(jn + 1), L.status, wait)) return;
     }
   }
   // Final R rows: each owner rewrites its rows of R (diagonal alpha, updated off-diagonals).
-  if (!grid_arrive_wait(L.bar, nb * (unsigned)(n + 1), L.status)) return;
+  if (!grid_arrive_wait(L.bar, nb * (unsigned)(n + 1), L.status, wait)) return;
   for (int64_t jr = row0; jr < row0 + nown && jr < n; ++jr) {
     const int64_t rl = jr - row0;
     for (int64_t c = jr + threadIdx.x; c <= n; c += blockDim.x) L.R[jr * ldw + c] = Wl[rl * ldw + c];
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(kQRThreads) qr64_kernel(const QRArgs a) {
       for (int64_t c = threadIdx.x; c < jr; c += blockDim.x) L.R[jr * ldw + c] = 0.0;
     return;
   }
-  if (!grid_arrive_wait(L.bar, nb * (unsigned)(n + 2), L.status)) return;
+  if (!grid_arrive_wait(L.bar, nb * (unsigned)(n + 2), L.status, wait)) return;
   if (b != 0) return;
   // Back substitution on CTA 0 (column-oriented): rhs in shared memory (reuses Wl).
   double* rhs = Wl;

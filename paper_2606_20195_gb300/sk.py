@@ -19,6 +19,7 @@ RULES = {"fp32": SK_FP32, "fp16_rn": SK_FP16_RN, "fp16_sr": SK_FP16_SR, "fp16_di
 SK_PARAM_CHUNK_ROWS, SK_PARAM_MODE, SK_PARAM_ROW_OFFSET, SK_PARAM_KERNEL = 1, 2, 3, 4
 SK_PARAM_TILE_COLS, SK_PARAM_THREADS, SK_PARAM_LAST_LAUNCHES, SK_PARAM_LAST_CHUNK_ROWS = 5, 6, 7, 8
 SK_PARAM_DEVICE_STATUS, SK_PARAM_LAST_KERNEL, SK_PARAM_SOLVE_GROUP_ROWS, SK_PARAM_LIST_CAP = 9, 10, 11, 12
+SK_PARAM_SCRATCH_LIMIT, SK_PARAM_SOLVE_WAIT_CYCLES, SK_PARAM_SCRATCH_BYTES = 13, 14, 15
 SK_MODE_ATOMIC, SK_MODE_DETERMINISTIC, SK_MODE_SERIAL_TILE = 0, 1, 2
 SK_KERNEL_AUTO, SK_KERNEL_TILE, SK_KERNEL_LITERAL, SK_KERNEL_OWNER, SK_KERNEL_GLOBAL = 0, 1, 2, 3, 4
 SK_KERNEL_REGISTER = 6
@@ -29,7 +30,7 @@ EXPORTS = [
     "sk_version", "sk_last_error", "sk_plan_create", "sk_plan_set", "sk_plan_get", "sk_apply",
     "sk_apply_host", "sk_solve", "sk_solve_status", "sk_solve_precond", "sk_materialize_S", "sk_batch_create",
     "sk_batch_set", "sk_batch_launch", "sk_batch_info", "sk_batch_destroy", "sk_destroy",
-    "sk_apply_noalloc", "sk_apply_typed",
+    "sk_apply_noalloc", "sk_apply_typed", "sk_apply_partials", "sk_finish_partials",
 ]
 
 
@@ -98,6 +99,10 @@ def load(path: str | None = None):
     L.sk_apply_noalloc.argtypes = [vp, vp, i64, i64, vp, vp]
     L.sk_apply_typed.restype = st
     L.sk_apply_typed.argtypes = [vp, vp, i32, i64, i64, vp, vp]
+    L.sk_apply_partials.restype = st
+    L.sk_apply_partials.argtypes = [vp, vp, i64, i64, vp, i64, i64, vp]
+    L.sk_finish_partials.restype = st
+    L.sk_finish_partials.argtypes = [vp, vp, i64, i64, i64, vp, vp]
     _lib = L
     return L
 
@@ -230,6 +235,14 @@ def sk_apply_noalloc(plan: int, A, lda: int, n: int, Y, stream=None) -> None:
     check(load().sk_apply_noalloc(plan, _ptr(A), lda, n, _ptr(Y), _stream_handle(stream)))
 
 
+def sk_apply_partials(plan: int, A, lda: int, n: int, P, t0: int, nchunks: int, stream=None) -> None:
+    check(load().sk_apply_partials(plan, _ptr(A), lda, n, _ptr(P), t0, nchunks, _stream_handle(stream)))
+
+
+def sk_finish_partials(plan: int, P, t0: int, nchunks: int, n: int, Y, stream=None) -> None:
+    check(load().sk_finish_partials(plan, _ptr(P), t0, nchunks, n, _ptr(Y), _stream_handle(stream)))
+
+
 # ----------------------------------------------------------------------------- convenience wrapper
 class Plan:
     """Owns an sk_plan handle; methods take torch CUDA tensors (marshalling only)."""
@@ -241,7 +254,8 @@ class Plan:
         self.handle = sk_plan_create(d, m, k, rule, seed)
         keys = {"chunk_rows": SK_PARAM_CHUNK_ROWS, "mode": SK_PARAM_MODE, "row_offset": SK_PARAM_ROW_OFFSET,
                 "kernel": SK_PARAM_KERNEL, "tile_cols": SK_PARAM_TILE_COLS, "threads": SK_PARAM_THREADS,
-                "solve_group_rows": SK_PARAM_SOLVE_GROUP_ROWS, "list_cap": SK_PARAM_LIST_CAP}
+                "solve_group_rows": SK_PARAM_SOLVE_GROUP_ROWS, "list_cap": SK_PARAM_LIST_CAP,
+                "scratch_limit": SK_PARAM_SCRATCH_LIMIT, "solve_wait_cycles": SK_PARAM_SOLVE_WAIT_CYCLES}
         for name, v in params.items():
             sk_plan_set(self.handle, keys[name], int(v))
 

@@ -16,7 +16,8 @@ from paper_2606_20195_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 RULES = [0, 1, 2, 3, 4]  # FP32, the three FP16 rules and bfloat16 round-to-nearest
-TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3, 4: 2e-2}
+# bfloat16 (rule 4): the FP16 bar scaled by the ratio of unit roundoffs, 2^-9 / 2^-12 = 8 (reading 13)
+TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3, 4: 1.6e-2}
 
 
 def _run(sk, A_h, d, k, rule, seed, dev, **params):

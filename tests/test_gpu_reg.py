@@ -4,7 +4,7 @@ totals and into Y in chunk order by the chunk-finish kernel (paper Sec. 4.1 scat
 
 Bars: on small-integer data every chunk total is exact, so the result is bit-exact with the oracle's
 canonical order for every rule, whatever the summation order inside a chunk; on random data it is
-within the atomic-mode tolerance of the FP64 sketch (1e-5 FP32, 2e-3 FP16 rules, 2e-2 bfloat16).
+within the atomic-mode tolerance of the FP64 sketch (1e-5 FP32, 2e-3 FP16 rules, 1.6e-2 bfloat16).
 The shapes cover: several chunks and slices, ragged column tiles (n not a multiple of 32 or of 4),
 block heights below, at and above the 1024 output rows of a work item (groups that hold several
 blocks, part of a block, or parts of two), d below 1024, a row offset and a row stride, and forced
@@ -20,7 +20,8 @@ from paper_2606_20195_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 RULES = [0, 1, 2, 3, 4]
-TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3, 4: 2e-2}
+# bfloat16 (rule 4): the FP16 bar scaled by the ratio of unit roundoffs, 2^-9 / 2^-12 = 8 (reading 13)
+TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3, 4: 1.6e-2}
 
 
 def _bits(Y, rule):

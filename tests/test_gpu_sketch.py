@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 
 RULES = [0, 1, 2, 3]
 RULES5 = [0, 1, 2, 3, 4]  # with the bfloat16 round-to-nearest rule
-TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3, 4: 2e-2}
+# bfloat16 (rule 4): the FP16 bar scaled by the ratio of unit roundoffs, 2^-9 / 2^-12 = 8 (reading 13)
+TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3, 4: 1.6e-2}
 
 
 def _to_np(Y, rule):

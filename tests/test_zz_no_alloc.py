@@ -41,7 +41,7 @@ def test_noalloc_matches_sk_apply_twice(sk, dev, rule, shape):
     assert oracle.rel_fro(ref, Y64) <= TOL[rule]
     Y1 = torch.full((d, n), 5.0, dtype=dt, device=dev)
     Y2 = torch.full((d, n), -3.0, dtype=dt, device=dev)
-    sk.sk_apply_noalloc(plan.handle, A, n, n, Y1)  # first call on the device sets up the address
+    sk.sk_apply_noalloc(plan.handle, A, n, n, Y1)  # first call on the device: its code may load here
     torch.cuda.synchronize()
     free_before, _ = torch.cuda.mem_get_info(dev)
     sk.sk_apply_noalloc(plan.handle, A, n, n, Y1)
@@ -55,6 +55,8 @@ def test_noalloc_matches_sk_apply_twice(sk, dev, rule, shape):
         assert oracle.rel_fro(got, ref) <= TOL[rule]
         assert oracle.rel_fro(got, Y64) <= TOL[rule]
     assert plan.get(sk.SK_PARAM_LAST_LAUNCHES) == apply_launches
+    # the no-allocation call's status word (in the static array) is readable and clear
+    assert plan.get(sk.SK_PARAM_DEVICE_STATUS) == 0
     plan.close()
 
 
