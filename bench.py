@@ -3,18 +3,24 @@
 Workload (default): the single-matrix sweep configuration m = 2^22, n = 64, d = 4096, k = 8,
 A FP32 iid N(0, 1) (the incoherent family), accumulation FP16 round-to-nearest (the headline rule);
 FP32 / stochastic / dithered / bfloat16 variants are timed beside it. A is 1 GiB, larger than the 129 MB L2,
-so no L2 flush is needed between steps. One step = one sk_apply (zero Y, the tile kernel, and the
-chunk-finish kernel when chunks are split into slices).
+so no L2 flush is needed between steps. One step = one sk_apply (zero Y, the kernel AUTO picks: the
+register kernel at this shape, and the chunk-finish kernel).
 
   value      device throughput, GB/s of (A read + Y written) with A resident in HBM
   e2e        the same metric through sk_apply_host with pinned host buffers (H2D of A and D2H of
              Y inside the timed region)
-  roofline   the tile kernel against the measured HBM copy bandwidth
+  roofline   the dominant kernel against the measured HBM copy bandwidth
   cpu_baseline  the CPU oracle (canonical FP16-RN sketch) on a bounded row sample, host cores
+
+Extras (default: serve, solve, batch): the batched uneven launch (256 matrices, one CUDA-graph
+replay), sketch-and-solve at 2^24 x 128, and the serving stream (reduced m range over 1000 requests,
+the full m range up to 2^24 over 200, and a saturated run with every request arriving at once).
 
 --impl reference times the oracle itself (the reference arm of this comparison) on the same
 workload, each step a bounded row sample. Under torchrun (N > 1) every rank sketches its own
-matrix (independent problems, weak scaling, no collective on the data path).
+matrix (independent problems, weak scaling, no collective on the data path), or, with --shard rows,
+the ranks share one matrix split by rows: each adds its FP32 chunk totals (sk_apply_partials), one
+NCCL all-reduce sums them and every rank finishes Y (sk_finish_partials) (strong scaling).
 """
 from __future__ import annotations
 
@@ -51,7 +57,15 @@ METRIC = "SA sketch HBM GB/s (% of peak) FP16 vs FP32 at equal distortion; p99 s
 KERNEL_SOURCES = ["paper_2606_20195_gb300/csrc/sk_tile.cuh", "paper_2606_20195_gb300/csrc/sk_tile_kernel.cuh",
                   "paper_2606_20195_gb300/csrc/sk_kernels.cu",
                   "paper_2606_20195_gb300/csrc/sk_own.cu",
+                  "paper_2606_20195_gb300/csrc/sk_reg.cu",
                   "paper_2606_20195_gb300/csrc/sk_device.cuh"]
+
+
+def default_chunk_rows(m: int) -> int:
+    """The library's default chunk length for an m-row matrix (at most 8 chunks, at least 4096 rows,
+    a multiple of 32): the row shards of one matrix must all use it."""
+    R = max(4096, (m + 7) // 8)
+    return (R + 31) // 32 * 32
 
 
 def y_dtype(rule: int):
@@ -592,9 +606,11 @@ def bench_batch(dev, rule_name="fp16_rn", count=256, reps=5):
             "tuned": params, "graph": True}
 
 
-def bench_serve(dev, count=1000, warm=200, log2_m=(14, 20), seed=0):
+def bench_serve(dev, count=1000, warm=200, log2_m=(14, 20), seed=0, rates=(0.5, 0.8, 0.95)):
     """Poisson stream of sketch-and-solve requests: continuous batching vs one at a time. Each
-    measured run serves `count` requests after a warm-up run of `warm` requests of the same mix."""
+    measured run serves `count` requests after a warm-up run of `warm` requests of the same mix; the
+    saturated run submits every request at t = 0 (throughput of the continuous path beside the
+    one-at-a-time path's back-to-back throughput)."""
     from paper_2606_20195_gb300 import serve
     one = serve.Server(slots=1, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
     one.run_one_at_a_time(serve.make_stream(warm, rate_hz=0.0, seed=seed + 1, log2_m=log2_m))
@@ -605,7 +621,11 @@ def bench_serve(dev, count=1000, warm=200, log2_m=(14, 20), seed=0):
                        f"n in 16..256, d=16n, k in {{1,4,8}}, 4 rules, 120 GB budget, 8 slots; "
                        f"{count} requests per run after {warm} warm-up requests",
            "one_at_a_time_back_to_back": cap}
-    for frac in (0.5, 0.8, 0.95):
+    srv = serve.Server(slots=8, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
+    srv.run(serve.make_stream(warm, rate_hz=0.0, seed=seed + 1, log2_m=log2_m))
+    out["saturated_continuous"] = srv.run(serve.make_stream(count, rate_hz=0.0, seed=seed, log2_m=log2_m))
+    srv.close()
+    for frac in rates:
         srv = serve.Server(slots=8, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
         # warm-up pass over the same mix (plan scratch and per-stream allocator pools)
         srv.run(serve.make_stream(warm, rate_hz=frac * capacity, seed=seed + 1, log2_m=log2_m))
@@ -619,6 +639,100 @@ def bench_serve(dev, count=1000, warm=200, log2_m=(14, 20), seed=0):
     return out
 
 
+def run_sharded(args, world, rank, dev, sk, inputs) -> int:
+    """One matrix split by rows over the ranks (strong scaling): per step every rank adds its rows'
+    FP32 chunk totals (sk_apply_partials), one NCCL all-reduce sums them, and every rank finishes Y
+    (sk_finish_partials)."""
+    import torch
+    import torch.distributed as dist
+    m, n, d, k = WORKLOADS[args.workload]
+    rule = sk.RULES[args.rule]
+    R = default_chunk_rows(m)
+    nchunks = (m + R - 1) // R
+    lo, hi = rank * m // world, (rank + 1) * m // world
+    A_pin = torch.from_numpy(inputs.host_matrix(hi - lo, n, "incoherent", seed=rank)).pin_memory()
+    A = A_pin.to(dev)
+    plan = sk.Plan(d, hi - lo, k, rule, seed=1234, row_offset=lo, chunk_rows=R)
+    full = sk.Plan(d, m, k, rule, seed=1234, chunk_rows=R)
+    P = torch.zeros((nchunks, d, n), dtype=torch.float32, device=dev)
+    Y = torch.empty((d, n), dtype=y_dtype(rule), device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(Ad):
+        sk.sk_apply_partials(plan.handle, Ad, n, n, P, 0, nchunks, stream)
+        if world > 1:
+            dist.all_reduce(P, op=dist.ReduceOp.SUM)
+        sk.sk_finish_partials(full.handle, P, 0, nchunks, n, Y, stream)
+
+    for _ in range(args.warmup):
+        step(A)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for _ in range(args.steps):
+            step(A)
+        evs[1].record(stream)
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    t = torch.tensor([evs[0].elapsed_time(evs[1])], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    es = 4 if rule == 0 else 2
+    bytes_step = m * n * 4 + d * n * es
+    value = bytes_step * args.steps / (max_ms * 1e-3) / 1e9
+    assert plan.get(sk.SK_PARAM_DEVICE_STATUS) == 0
+    launches = plan.get(sk.SK_PARAM_LAST_LAUNCHES) + full.get(sk.SK_PARAM_LAST_LAUNCHES)
+    # e2e: this rank's rows copied in from pinned host memory every step, Y copied out
+    Y_pin = torch.empty((d, n), dtype=y_dtype(rule)).pin_memory()
+    A_in = torch.empty_like(A)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        A_in.copy_(A_pin, non_blocking=True)
+        step(A_in)
+        Y_pin.copy_(Y, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    te = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs") or 6800.0
+    achieved = bytes_step / world / (max_ms / args.steps * 1e-3) / 1e9  # per-GPU share of the bytes
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32+f16" if rule != 0 else "f32",
+            "data": "synthetic (seeded iid N(0,1) rows, one matrix split by rows over the ranks)",
+            "config": {"workload": args.workload, "m": m, "n": n, "d": d, "k": k, "rule": args.rule,
+                       "chunk_rows": R, "l2": "inputs larger than L2, no flush" if m * n * 4 > 129e6 else "inputs below L2",
+                       "parallelism": f"rows{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "note": "per-GPU share of the step (partials + all-reduce + finish)"},
+            "cpu_baseline": None,
+            "e2e": {"value": bytes_step / float(te.item()) / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": (hi - lo) * n * 4, "d2h_bytes_per_step": d * n * es},
+            "gpu_launches": launches * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    full.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -628,8 +742,10 @@ def main() -> int:
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--rule", default="fp16_rn", choices=["fp32", "fp16_rn", "fp16_sr", "fp16_dither", "bf16_rn"])
     ap.add_argument("--no-extras", action="store_true", help="skip variants, distortion, cpu baseline, serving")
-    ap.add_argument("--extras", default="serve",
-                    help="comma list of extra measurements: serve (default), solve, batch, all")
+    ap.add_argument("--extras", default="serve,solve,batch",
+                    help="comma list of extra measurements: serve, solve, batch (the default), paper, all")
+    ap.add_argument("--shard", default="none", choices=["none", "rows"],
+                    help="rows: the ranks share one matrix split by rows (partials, NCCL all-reduce, finish)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_init()
@@ -648,6 +764,8 @@ def main() -> int:
     if world > 1:
         dist.barrier()
     sk.load()
+    if args.shard == "rows":
+        return run_sharded(args, world, rank, dev, sk, inputs)
 
     m, n, d, k = WORKLOADS[args.workload]
     rule = sk.RULES[args.rule]
@@ -684,8 +802,8 @@ def main() -> int:
     launches_per_step = plan.get(sk.SK_PARAM_LAST_LAUNCHES)
     R_used = plan.get(sk.SK_PARAM_LAST_CHUNK_ROWS)
     kernel_name = {sk.SK_KERNEL_TILE: "tile_kernel", sk.SK_KERNEL_OWNER: "own_kernel",
-                   sk.SK_KERNEL_LITERAL: "literal_kernel", sk.SK_KERNEL_GLOBAL: "global_kernel"}.get(
-                       plan.get(sk.SK_PARAM_LAST_KERNEL), "det_kernel")
+                   sk.SK_KERNEL_LITERAL: "literal_kernel", sk.SK_KERNEL_GLOBAL: "global_kernel",
+                   sk.SK_KERNEL_REGISTER: "reg_kernel"}.get(plan.get(sk.SK_PARAM_LAST_KERNEL), "det_kernel")
     t = torch.tensor([total_ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -738,8 +856,9 @@ def main() -> int:
                 "traffic": traffic_record(kernel_name, args.workload, args.rule), "peak_source": peak_note,
                 "kernel": f"sk::{kernel_name}<{args.rule}>",
                 "algorithmic_bytes_per_launch": bytes_step}
-    # The second ceiling of this path: signed FP32 updates (m n k per launch, k/4 per byte of A),
-    # executed as shared-memory reductions; reported per SM clock beside the HBM fraction.
+    # The second ceiling of this path: signed FP32 updates (m n k per launch, k/4 per byte of A); in
+    # the register kernel every update is a packed FMA on a row staged in shared memory, so the rate of
+    # shared-memory row reads bounds it. Reported per SM clock beside the HBM fraction.
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     upd_s = m * n * k / (avg_launch_ms * 1e-3)
     sm_hz = (clocks.get("sm_mhz") or 0) * 1e6
@@ -803,6 +922,8 @@ def main() -> int:
         if "serve" in want:
             extras["serving"] = bench_serve(dev)
             extras["p99_solve_ms"] = extras["serving"]["rate_80pct"]["continuous"]["p99_ms"]
+            # the serving configuration's full m range (up to 2^24 rows: up to 16 GB of A per request)
+            extras["serving_full_m_range"] = bench_serve(dev, count=200, warm=40, log2_m=(14, 24), rates=(0.8,))
         if "solve" in want:
             extras["sketch_and_solve"] = bench_solve(dev)
         if "batch" in want:

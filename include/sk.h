@@ -125,7 +125,13 @@ typedef enum {
    * SK_ERR_TIMEOUT; small values exist to exercise that path. */
   SK_PARAM_SOLVE_WAIT_CYCLES = 14,
   /* Read-only: bytes of device scratch the plan holds now. */
-  SK_PARAM_SCRATCH_BYTES = 15
+  SK_PARAM_SCRATCH_BYTES = 15,
+  /* m, the rows of A the plan's calls process (set at sk_plan_create; may be changed between calls).
+   * S is a function of (seed, global row, block), so a plan serves matrices of any height with the
+   * same S restricted to their rows; the default chunk length follows m. Its scratch is kept and
+   * grown as needed, so one plan can serve a stream of requests of varying m without allocating
+   * once it has seen the largest. */
+  SK_PARAM_ROWS = 16
 } sk_param;
 
 enum { SK_MODE_ATOMIC = 0, SK_MODE_DETERMINISTIC = 1, SK_MODE_SERIAL_TILE = 2 };

@@ -622,6 +622,11 @@ sk_status sk_plan_set(sk_plan p, int32_t key, int64_t v) {
       if (v < 0 || v > 64) return set_error(SK_ERR_INVALID_ARG, "list capacity must be in [0, 64]");
       p->list_cap = (int32_t)v;
       return SK_OK;
+    case SK_PARAM_ROWS:
+      if (v < 1) return set_error(SK_ERR_INVALID_ARG, "rows must be >= 1");
+      if (v > ((int64_t)1 << 56)) return set_error(SK_ERR_UNSUPPORTED, "rows=%lld too large", (long long)v);
+      p->m = v;
+      return SK_OK;
     case SK_PARAM_SCRATCH_LIMIT:
       if (v < 0) return set_error(SK_ERR_INVALID_ARG, "scratch limit must be >= 0");
       p->scratch_limit = v;
@@ -648,6 +653,7 @@ sk_status sk_plan_get(sk_plan p, int32_t key, int64_t* v) {
     case SK_PARAM_SOLVE_GROUP_ROWS: *v = p->solve_group_rows; return SK_OK;
     case SK_PARAM_LIST_CAP: *v = p->list_cap; return SK_OK;
     case SK_PARAM_SCRATCH_LIMIT: *v = p->scratch_limit; return SK_OK;
+    case SK_PARAM_ROWS: *v = p->m; return SK_OK;
     case SK_PARAM_SOLVE_WAIT_CYCLES: *v = p->solve_wait_cycles; return SK_OK;
     case SK_PARAM_SCRATCH_BYTES: *v = (int64_t)plan_scratch_bytes(p); return SK_OK;
     case SK_PARAM_LAST_LAUNCHES: *v = p->last_launches; return SK_OK;

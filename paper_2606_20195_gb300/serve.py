@@ -4,11 +4,16 @@ Requests arrive over time (a Poisson stream in the benchmark). The server keeps 
 slots, each a CUDA stream, and an HBM budget. A waiting request is admitted as soon as a slot is free
 and its device footprint fits the budget; admitted requests run concurrently on their streams, so
 requests that arrive while others are on the GPU overlap with them. Plans (and the device scratch
-they own: sketches, FP64 QR workspace, chunk buffers) are cached per (d, m, k, rule) and reused by
-later requests of the same shape. Latency is measured from arrival to the moment x is ready.
+they own: sketches, FP64 QR workspace, chunk buffers) are cached per (d, k, rule) and reused by later
+requests of any height (SK_PARAM_ROWS sets a request's m on the cached plan), so once the scratch has
+grown to the largest request seen, serving allocates no device memory: a cudaMalloc in the middle of
+the stream would synchronize every slot's stream. Latency is measured from arrival to the moment x is
+ready.
 
-Each request's matrix is materialized on the device when it is admitted (synthetic workloads; the
-same seeded families the tests and benchmarks use), so upload cost is part of its service time.
+Each request's matrix is materialized on the device by a seeded generator when it is admitted
+(synthetic workloads; the same families the tests and benchmarks use). That generation stands in for
+the client's data arriving and is part of the request's service time; a host-to-device upload is not
+modelled (at the host link's ~210 GB/s it would dominate every request larger than a few MB).
 """
 from __future__ import annotations
 
@@ -53,7 +58,8 @@ def footprint_bytes(req: Request) -> int:
 
 
 def plan_scratch_bytes(req: Request) -> int:
-    """Device scratch a cached plan keeps: sketches, FP64 QR workspace, chunk buffers."""
+    """Estimate of the device scratch a plan needs for a request (before it has run): sketches, FP64
+    QR workspace, chunk totals. After a request the server reads the plan's actual scratch instead."""
     es = 4 if req.rule == skb.SK_FP32 else 2
     sketches = req.d * (req.n + 1) * es
     qr = 8 * (2 * req.n * (req.n + 1) + 2 * req.n) + 4096
@@ -92,7 +98,7 @@ class Server:
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
         self.free_slots = list(range(slots))
         self.used_bytes = 0
-        self.plans: dict = {}        # (d, m, k, rule) -> list of [Plan, busy]
+        self.plans: dict = {}        # (d, k, rule) -> list of [Plan, busy, scratch bytes]
         self.resident_bytes = 0      # device scratch kept by cached plans
         self.deterministic = deterministic
         self.keep_results = keep_results
@@ -100,22 +106,28 @@ class Server:
 
     # ------------------------------------------------------------------ plans
     def _plan(self, req: Request):
-        key = (req.d, req.m, req.k, req.rule)
+        key = (req.d, req.k, req.rule)
         pool = self.plans.setdefault(key, [])
         for idx, entry in enumerate(pool):
             if not entry[1]:
                 entry[1] = True
+                entry[0].set(skb.SK_PARAM_ROWS, req.m)
                 return entry[0], (key, idx)
         mode = skb.SK_MODE_DETERMINISTIC if self.deterministic else skb.SK_MODE_ATOMIC
-        # The sketch seed is derived from the shape, so a cached plan serves every request of it.
-        seed = (req.d * 1000003 + req.m * 97 + req.k * 13 + req.rule) & 0xFFFFFFFF
+        # The sketch seed is derived from (d, k, rule), so a cached plan serves every request of them.
+        seed = (req.d * 1000003 + req.k * 13 + req.rule) & 0xFFFFFFFF
         plan = skb.Plan(req.d, req.m, req.k, req.rule, seed=seed, mode=mode)
-        pool.append([plan, True])
-        self.resident_bytes += plan_scratch_bytes(req)
+        est = plan_scratch_bytes(req)
+        pool.append([plan, True, est])
+        self.resident_bytes += est
         return plan, (key, len(pool) - 1)
 
     def _release_plan(self, key):
-        self.plans[key[0]][key[1]][1] = False
+        entry = self.plans[key[0]][key[1]]
+        entry[1] = False
+        actual = entry[0].get(skb.SK_PARAM_SCRATCH_BYTES)  # what the plan holds now
+        self.resident_bytes += actual - entry[2]
+        entry[2] = actual
 
     # ------------------------------------------------------------------ one request
     def _launch(self, req: Request, slot: int):
@@ -221,8 +233,7 @@ class Server:
                     keep.append(entry)
                 else:
                     entry[0].close()
-                    d, m, k, rule = key
-                    self.resident_bytes -= plan_scratch_bytes(Request(-1, m, 0, d, k, rule, "", 0))
+                    self.resident_bytes -= entry[2]
             self.plans[key] = keep
         self.resident_bytes = max(self.resident_bytes, 0)
 

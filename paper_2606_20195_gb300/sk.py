@@ -19,7 +19,7 @@ RULES = {"fp32": SK_FP32, "fp16_rn": SK_FP16_RN, "fp16_sr": SK_FP16_SR, "fp16_di
 SK_PARAM_CHUNK_ROWS, SK_PARAM_MODE, SK_PARAM_ROW_OFFSET, SK_PARAM_KERNEL = 1, 2, 3, 4
 SK_PARAM_TILE_COLS, SK_PARAM_THREADS, SK_PARAM_LAST_LAUNCHES, SK_PARAM_LAST_CHUNK_ROWS = 5, 6, 7, 8
 SK_PARAM_DEVICE_STATUS, SK_PARAM_LAST_KERNEL, SK_PARAM_SOLVE_GROUP_ROWS, SK_PARAM_LIST_CAP = 9, 10, 11, 12
-SK_PARAM_SCRATCH_LIMIT, SK_PARAM_SOLVE_WAIT_CYCLES, SK_PARAM_SCRATCH_BYTES = 13, 14, 15
+SK_PARAM_SCRATCH_LIMIT, SK_PARAM_SOLVE_WAIT_CYCLES, SK_PARAM_SCRATCH_BYTES, SK_PARAM_ROWS = 13, 14, 15, 16
 SK_MODE_ATOMIC, SK_MODE_DETERMINISTIC, SK_MODE_SERIAL_TILE = 0, 1, 2
 SK_KERNEL_AUTO, SK_KERNEL_TILE, SK_KERNEL_LITERAL, SK_KERNEL_OWNER, SK_KERNEL_GLOBAL = 0, 1, 2, 3, 4
 SK_KERNEL_REGISTER = 6
