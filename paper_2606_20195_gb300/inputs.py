@@ -67,6 +67,27 @@ def device_matrix(m: int, n: int, family: str = "incoherent", seed: int = 0, dev
     raise ValueError(f"unknown family {family!r}")
 
 
+def fill_device_matrix(out, family: str = "incoherent", seed: int = 0):
+    """device_matrix written into an existing float32 CUDA tensor (same values for the same seed and
+    shape): no device allocation, for callers that place matrices in their own memory."""
+    import torch
+    g = torch.Generator(device=out.device)
+    g.manual_seed(seed)
+    m, n = out.shape
+    if family == "incoherent":
+        torch.randn((m, n), generator=g, out=out)
+        return out
+    if family == "coherent":
+        torch.randn((m, n), generator=g, out=out)
+        out.mul_(1e-3)
+        q = min(m, n)
+        out[:q, :] = 0.0
+        idx = torch.arange(q, device=out.device)
+        out[idx, idx] = 1e3
+        return out
+    raise ValueError(f"unknown family {family!r} for an in-place fill")
+
+
 def ls_problem_host(m: int, n: int, family: str = "coherent", seed: int = 0, noise: float = 1e-6):
     """(A, b, x_star) with b = A x_star + noise * N(0, 1), float32 (sketch-and-solve workload)."""
     A = host_matrix(m, n, family, seed)

@@ -10,6 +10,11 @@ grown to the largest request seen, serving allocates no device memory: a cudaMal
 the stream would synchronize every slot's stream. Latency is measured from arrival to the moment x is
 ready.
 
+Device memory for requests comes from one arena: a buffer the size of the HBM budget, allocated when
+the server starts, in which every admitted request's A, b and x get a range (first fit, freed when
+the request completes). Admission needs both a free slot and a range; serving itself never calls the
+CUDA allocator, whose cudaMalloc / cudaFree of multi-GB blocks would synchronize every slot's stream.
+
 Each request's matrix is materialized on the device by a seeded generator when it is admitted
 (synthetic workloads; the same families the tests and benchmarks use). That generation stands in for
 the client's data arriving and is part of the request's service time; a host-to-device upload is not
@@ -87,6 +92,56 @@ def make_stream(count: int, rate_hz: float, seed: int = 0, log2_m=(14, 24), ns=(
     return out
 
 
+class Arena:
+    """First-fit ranges of one float32 device buffer, 256-byte aligned, coalesced on release."""
+
+    ALIGN = 64  # floats
+
+    def __init__(self, floats: int, device):
+        import torch
+        self.size = max(int(floats) // self.ALIGN * self.ALIGN, self.ALIGN)
+        self.buf = torch.empty(self.size, dtype=torch.float32, device=device)
+        self.free = [(0, self.size)]  # (offset, length), sorted by offset, disjoint, not adjacent
+
+    def _round(self, n: int) -> int:
+        return max((int(n) + self.ALIGN - 1) // self.ALIGN * self.ALIGN, self.ALIGN)
+
+    def alloc(self, n: int):
+        """Offset of a range of n floats, or None if no free range is long enough."""
+        n = self._round(n)
+        for i, (o, ln) in enumerate(self.free):
+            if ln >= n:
+                if ln == n:
+                    del self.free[i]
+                else:
+                    self.free[i] = (o + n, ln - n)
+                return o
+        return None
+
+    def release(self, o: int, n: int) -> None:
+        n = self._round(n)
+        i = 0
+        while i < len(self.free) and self.free[i][0] < o:
+            i += 1
+        self.free.insert(i, (o, n))
+        # merge with the next and the previous range when they touch
+        if i + 1 < len(self.free) and self.free[i][0] + self.free[i][1] == self.free[i + 1][0]:
+            self.free[i] = (o, self.free[i][1] + self.free[i + 1][1])
+            del self.free[i + 1]
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == self.free[i][0]:
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            del self.free[i]
+
+    def view(self, o: int, shape):
+        numel = 1
+        for v in shape:
+            numel *= v
+        return self.buf[o:o + numel].view(*shape)
+
+    def free_floats(self) -> int:
+        return sum(ln for _, ln in self.free)
+
+
 class Server:
     def __init__(self, slots: int = 8, hbm_budget_bytes: int = 120 * 10**9, device: str = "cuda:0",
                  deterministic: bool = False, keep_results: bool = True):
@@ -103,6 +158,7 @@ class Server:
         self.deterministic = deterministic
         self.keep_results = keep_results
         self.peak_bytes = 0
+        self.arena = Arena(self.budget // 4, self.device)
 
     # ------------------------------------------------------------------ plans
     def _plan(self, req: Request):
@@ -130,21 +186,38 @@ class Server:
         entry[2] = actual
 
     # ------------------------------------------------------------------ one request
-    def _launch(self, req: Request, slot: int):
+    def _place(self, req: Request):
+        """Arena ranges for A (m x n), b (m) and x plus x* (2n); None if they do not all fit."""
+        got = []
+        for numel in (req.m * req.n, req.m, 2 * req.n):
+            o = self.arena.alloc(numel)
+            if o is None:
+                for o2, n2 in got:
+                    self.arena.release(o2, n2)
+                return None
+            got.append((o, numel))
+        return got
+
+    def _launch(self, req: Request, slot: int, ranges):
         torch = self.torch
         st = self.streams[slot]
+        (oa, _), (ob, _), (ox, _) = ranges
+        A = self.arena.view(oa, (req.m, req.n))
+        b = self.arena.view(ob, (req.m,))
+        x = self.arena.view(ox, (req.n,))
+        xs = self.arena.view(ox + Arena.ALIGN * ((req.n + Arena.ALIGN - 1) // Arena.ALIGN), (req.n,))
         with torch.cuda.stream(st):
-            A = inputs.device_matrix(req.m, req.n, req.family, seed=req.seed, device=str(self.device))
+            inputs.fill_device_matrix(A, req.family, seed=req.seed)
             g = torch.Generator(device=self.device)
             g.manual_seed(req.seed + 7)
-            xs = torch.randn(req.n, generator=g, device=self.device)
-            b = A @ xs + 1e-6 * torch.randn(req.m, generator=g, device=self.device)
-            x = torch.empty(req.n, dtype=torch.float32, device=self.device)
+            torch.randn(req.n, generator=g, out=xs)
+            torch.randn(req.m, generator=g, out=b)
+            b.mul_(1e-6).addmv_(A, xs)  # b = A x* + 1e-6 N(0, 1)
             plan, key = self._plan(req)
             skb.sk_solve(plan.handle, A, req.n, req.n, b, x, st)
             ev = torch.cuda.Event()
             ev.record(st)
-        return {"req": req, "slot": slot, "A": A, "b": b, "x": x, "plan": plan, "key": key, "event": ev}
+        return {"req": req, "slot": slot, "ranges": ranges, "x": x, "plan": plan, "key": key, "event": ev}
 
     def _finish(self, job, now: float):
         req = job["req"]
@@ -153,6 +226,8 @@ class Server:
         req.status, req.kappa = status, kappa
         if self.keep_results:
             req.x = job["x"].cpu()
+        for o, numel in job["ranges"]:
+            self.arena.release(o, numel)
         self._release_plan(job["key"])
         self.free_slots.append(job["slot"])
         self.used_bytes -= footprint_bytes(req)
@@ -193,12 +268,15 @@ class Server:
                     self._evict_idle_plans()
                     if self.used_bytes + self.resident_bytes + fb + plan_scratch_bytes(req) > self.budget:
                         break
+                ranges = self._place(req)
+                if ranges is None:  # no contiguous range in the arena yet: wait for completions
+                    break
                 heapq.heappop(waiting)
                 slot = self.free_slots.pop(0)
                 self.used_bytes += fb
                 self.peak_bytes = max(self.peak_bytes, self.used_bytes + self.resident_bytes)
                 req.admitted = clock() - t0
-                running.append(self._launch(req, slot))
+                running.append(self._launch(req, slot, ranges))
             if not running and not waiting and i < len(pending):
                 # idle until the next arrival
                 delay = pending[i].arrival - (clock() - t0)
@@ -219,7 +297,10 @@ class Server:
                 time.sleep(req.arrival - now)
             self.used_bytes += footprint_bytes(req)
             req.admitted = clock() - t0
-            job = self._launch(req, self.free_slots.pop(0))
+            ranges = self._place(req)
+            if ranges is None:
+                raise ValueError(f"request {req.rid} does not fit in the arena")
+            job = self._launch(req, self.free_slots.pop(0), ranges)
             job["event"].synchronize()
             self._finish(job, clock() - t0)
         return summarize(requests, clock() - t0)
@@ -243,6 +324,7 @@ class Server:
                 entry[0].close()
         self.plans.clear()
         self.resident_bytes = 0
+        self.arena = None
 
 
 def summarize(requests: list[Request], wall_s: float) -> dict:
