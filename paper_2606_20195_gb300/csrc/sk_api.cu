@@ -241,7 +241,7 @@ bool choose_reg(const sk_plan_s* p, int64_t n, int64_t rows, const DevInfo& di, 
   }
   const size_t optin = (size_t)std::min(di.optin, 232448) - 1024;
   int32_t nsub = 0, cap = 0;
-  if (!reg_choose_box(p->B, optin, p->list_cap, &nsub, &cap)) return false;
+  if (!reg_choose_box(p->d, p->B, optin, p->list_cap, &nsub, &cap)) return false;
   const int64_t R = p->R > 0 ? p->R : default_chunk_rows(p->m);
   const int64_t ncg = (n + 31) / 32;
   const int64_t ntg = (p->d + reg_targets() - 1) / reg_targets();

@@ -67,14 +67,16 @@ void global_passes(const TileLaunch& L, int64_t* ns, int64_t* cb);
 int64_t launch_P_floats(const TileLaunch& L);
 // The global-accumulator kernel and its chunk finish, in passes (sk_global.cu); needs L.P.
 cudaError_t launch_global(const TileLaunch& L, cudaStream_t st, int32_t* launches);
-// Register kernel (sk_reg.cu): shared-memory bytes for a box of nsub TMA copies and lists of cap
-// entries; threads per CTA; output rows per work item; the box and capacity for block height B within
-// `smem_limit` bytes (cap_fixed > 0 imposes the capacity; false if nothing fits); and the launch (its
-// chunk finish included; needs L.P).
-size_t reg_smem_bytes(int32_t nsub, int32_t cap);
+// Register kernel (sk_reg.cu): shared-memory bytes for a box of nsub TMA copies, lists of cap entries
+// and overflow lists of ovf_cap entries; threads per CTA; output rows per work item; blocks of S that
+// reach the widest group of output rows; the box and capacity for a sketch of d rows and block height
+// B within `smem_limit` bytes (cap_fixed > 0 imposes the capacity; false if nothing fits); and the
+// launch (its chunk finish included; needs L.P).
+size_t reg_smem_bytes(int32_t nsub, int32_t cap, int32_t ovf_cap);
 int32_t reg_threads();
 int32_t reg_targets();
-bool reg_choose_box(int64_t B, size_t smem_limit, int32_t cap_fixed, int32_t* nsub, int32_t* cap);
+int32_t reg_blocks_per_group(int64_t d, int64_t B);
+bool reg_choose_box(int64_t d, int64_t B, size_t smem_limit, int32_t cap_fixed, int32_t* nsub, int32_t* cap);
 cudaError_t launch_reg(const TileLaunch& L, cudaStream_t st, int32_t* launches);
 // Resident CTAs per SM of the tile kernel for (rule, threads, dynamic shared memory).
 int32_t tile_ctas_per_sm(int32_t rule, int32_t threads, size_t smem);
