@@ -186,10 +186,16 @@ class Server:
         entry[2] = actual
 
     # ------------------------------------------------------------------ one request
+    @staticmethod
+    def _xs_offset(n: int) -> int:
+        """Offset of x* within the x range: x, then x* at the next aligned position."""
+        return Arena.ALIGN * ((n + Arena.ALIGN - 1) // Arena.ALIGN)
+
     def _place(self, req: Request):
-        """Arena ranges for A (m x n), b (m) and x plus x* (2n); None if they do not all fit."""
+        """Arena ranges for A (m x n), b (m) and x followed by x* (each at an aligned start); None if
+        they do not all fit."""
         got = []
-        for numel in (req.m * req.n, req.m, 2 * req.n):
+        for numel in (req.m * req.n, req.m, self._xs_offset(req.n) + req.n):
             o = self.arena.alloc(numel)
             if o is None:
                 for o2, n2 in got:
@@ -205,7 +211,7 @@ class Server:
         A = self.arena.view(oa, (req.m, req.n))
         b = self.arena.view(ob, (req.m,))
         x = self.arena.view(ox, (req.n,))
-        xs = self.arena.view(ox + Arena.ALIGN * ((req.n + Arena.ALIGN - 1) // Arena.ALIGN), (req.n,))
+        xs = self.arena.view(ox + self._xs_offset(req.n), (req.n,))
         with torch.cuda.stream(st):
             inputs.fill_device_matrix(A, req.family, seed=req.seed)
             g = torch.Generator(device=self.device)

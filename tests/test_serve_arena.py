@@ -25,3 +25,19 @@ def test_arena_first_fit_alignment_and_coalescing():
     assert ar.free == [(0, 10 * U)]          # everything merged back into one range
     v = ar.view(ar.alloc(12), (3, 4))
     assert tuple(v.shape) == (3, 4)
+
+
+def test_x_and_xstar_stay_inside_their_range():
+    # A request's x and x* share one arena range: x at its start, x* at the next aligned offset. The
+    # range must hold both, or x* would overwrite whatever the arena placed after it (another
+    # request's A or b while both run).
+    srv = object.__new__(serve.Server)  # placement only: no streams, no device
+    srv.arena = serve.Arena(serve.Arena.ALIGN * 1000, "cpu")
+    for n in (1, 16, 32, 63, 64, 65, 100, 256):
+        req = serve.Request(rid=0, m=128, n=n, d=16 * n, k=4, rule=0, family="incoherent", seed=0)
+        ranges = srv._place(req)
+        (ox, nx) = ranges[2]
+        assert srv._xs_offset(n) >= n                        # x* starts after x
+        assert srv._xs_offset(n) + n <= srv.arena._round(nx)  # and ends inside the range
+        for o, numel in ranges:
+            srv.arena.release(o, numel)
