@@ -618,7 +618,8 @@ def bench_serve(dev, count=1000, warm=200, log2_m=(14, 20), seed=0, rates=(0.5, 
     capacity = cap["solves_per_s"]
     one.close()
     out = {"workload": f"Poisson sketch-and-solve requests, m log-uniform [2^{log2_m[0]},2^{log2_m[1]}], "
-                       f"n in 16..256, d=16n, k in {{1,4,8}}, 4 rules, 120 GB budget, 8 slots; "
+                       f"n in 16..256, d=16n, k in {{1,4,8}}, 4 rules, 120 GB budget, 8 slots; continuous path: one batched "
+                       f"sketch launch per rule and scheduling step, then per-request FP64 QR; "
                        f"{count} requests per run after {warm} warm-up requests",
            "one_at_a_time_back_to_back": cap}
     srv = serve.Server(slots=8, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)

@@ -131,7 +131,12 @@ typedef enum {
    * same S restricted to their rows; the default chunk length follows m. Its scratch is kept and
    * grown as needed, so one plan can serve a stream of requests of varying m without allocating
    * once it has seen the largest. */
-  SK_PARAM_ROWS = 16
+  SK_PARAM_ROWS = 16,
+  /* Batch only (sk_batch_set): chunk length of every item from its own m alone, at most this many
+   * chunks per matrix and at least 4096 rows (a multiple of 256), instead of the tuning that looks at
+   * the whole batch. A request's chunking, hence its rounding, then does not depend on what else is
+   * in the batch (0, the default: tuned over the batch; SK_PARAM_CHUNK_ROWS, if set, wins). */
+  SK_PARAM_ITEM_CHUNKS = 17
 } sk_param;
 
 enum { SK_MODE_ATOMIC = 0, SK_MODE_DETERMINISTIC = 1, SK_MODE_SERIAL_TILE = 2 };
@@ -224,7 +229,22 @@ SK_API sk_status sk_apply_host(sk_plan plan, const float* A_host, int64_t lda, i
 SK_API sk_status sk_solve(sk_plan plan, const float* A_dev, int64_t lda, int64_t n, const float* b_dev, float* x_dev,
                    void* stream);
 
-/* Status of the last sk_solve on this plan: synchronizes `stream`, then reads the device status
+/*
+ * sk_solve_sketched — the FP64 back end of sk_solve on a sketch the caller already holds (paper
+ * Sec. 5.1: QR of S A, then x from R x = (Q^T S b)[:n]). For services that form the sketches of many
+ * requests in one batched launch (sk_batch_launch over [A_i | b_i]) and then solve each.
+ *   SAb_dev: device, d x (n+1) values of the plan's output type (FP32 for SK_FP32, binary16 or
+ *     bfloat16 otherwise), row-major with row stride ld >= n + 1 elements: columns 0..n-1 are S A,
+ *     column n is S b. Read only. d is the plan's d; requires n <= d and n <= 1024.
+ *   x_dev: device, n floats (output).
+ * Uses and grows the plan's FP64 workspace as sk_solve does (no allocation once it has seen this n);
+ * the plan's m, k and seed play no part. Status and kappa: sk_solve_status. Errors: as sk_solve,
+ * synchronously for arguments; nothing is enqueued on an error.
+ */
+SK_API sk_status sk_solve_sketched(sk_plan plan, const void* SAb_dev, int64_t ld, int64_t n, float* x_dev,
+                                   void* stream);
+
+/* Status of the last sk_solve or sk_solve_sketched on this plan: synchronizes `stream`, then reads the device status
  * word. SK_ERR_NUMERIC: SA was rank deficient (zero pivot; x was set to NaN). SK_ERR_TIMEOUT: a
  * grid barrier of the QR kernel gave up waiting. Also writes the FP64 estimate
  * kappa(SA) ~ max|R_ii| / min|R_ii| (>= 1) if kappa != NULL. */
@@ -279,8 +299,15 @@ typedef struct sk_batch_s* sk_batch;
  * from the tuning table unless overridden by sk_batch_set, and uploads the work list.
  * Allocates device memory for the work list (kept by the batch). */
 SK_API sk_status sk_batch_create(const sk_batch_item* items, int32_t count, int32_t rule, sk_batch* out);
-/* Override the tile choice: key is SK_PARAM_TILE_COLS, SK_PARAM_THREADS or SK_PARAM_CHUNK_ROWS;
- * must be called before the first sk_batch_launch. */
+/* Replace the items of a batch (same rule and overrides). The next sk_batch_launch rebuilds the
+ * work list and uploads it on its stream, reusing the batch's device buffers when they are large
+ * enough (they grow otherwise), so a service that sketches a new set of requests at every
+ * scheduling step keeps one batch object per rule instead of creating and destroying one per step
+ * (sk_batch_destroy synchronizes the device). The previous launch of this batch must have
+ * completed (its work list is overwritten in place). */
+SK_API sk_status sk_batch_rebind(sk_batch batch, const sk_batch_item* items, int32_t count);
+/* Override the tile choice: key is SK_PARAM_TILE_COLS, SK_PARAM_THREADS, SK_PARAM_CHUNK_ROWS or
+ * SK_PARAM_ITEM_CHUNKS; must be called before the first sk_batch_launch after a create or a rebind. */
 SK_API sk_status sk_batch_set(sk_batch batch, int32_t key, int64_t value);
 /* Zero every Y_i and run the persistent kernel on `stream`: no allocation, no host sync, so the
  * call can be captured into a CUDA graph and replayed. */

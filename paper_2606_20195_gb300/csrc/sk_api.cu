@@ -863,52 +863,21 @@ int64_t solve_group_cap(const sk_plan_s* p, int64_t n, const DevInfo& di) {
   if (p->d > cap && cap < 2 * n) return 0;
   return cap;
 }
-}  // namespace
 
-sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const float* b, float* x, void* stream) {
-  clear_error();
-  sk_status s = validate_apply(p, A, lda, n, x);
-  if (s != SK_OK) return s;
-  if (!b) return set_error(SK_ERR_INVALID_ARG, "b is NULL");
-  if (n > p->d) return set_error(SK_ERR_INVALID_ARG, "sketch-and-solve needs n=%lld <= d=%lld", (long long)n, (long long)p->d);
-  if (n > kMaxSolveN) return set_error(SK_ERR_UNSUPPORTED, "sketch-and-solve supports n <= %d", kMaxSolveN);
-  DevInfo di;
-  s = dev_info(&di);
-  if (s != SK_OK) return s;
-  const int64_t cap = solve_group_cap(p, n, di);
-  if (cap < 1)
-    return set_error(SK_ERR_UNSUPPORTED, "FP64 QR of a %lld x %lld sketch: too many columns for shared memory",
-                     (long long)p->d, (long long)(n + 1));
-  const int64_t groups1 = (p->d > cap) ? (p->d + cap - 1) / cap : 0;
-  const SolveLayout Lo = solve_layout(p->d, n, p->rule, groups1);
-  if (p->solve_bytes < Lo.total) {
-    s = plan_grow(p, &p->solve_buf, &p->solve_bytes, Lo.total, "sketch-and-solve scratch");
-    if (s != SK_OK) return s;
-    cudaMemset(p->solve_buf, 0, Lo.total);
-  }
-  p->solve_status_off = Lo.status;
-  p->solve_kappa_off = Lo.kappa;
+// QR back end of sketch-and-solve (paper Sec. 5.3: QR of the sketch SA, then R x = (Q^T Sb)[:n]):
+// x from the sketch columns SA (d x n, row stride lda_sa) and Sb (d values, stride sb_stride) in the
+// plan's element type, in FP64; tree levels (groups of at most `cap` rows factored, their [R | c]
+// factors stacked and factored again) when the sketch is taller than one QR launch holds.
+sk_status solve_backend(sk_plan_s* p, const void* SA, int64_t lda_sa, const void* Sb, int64_t sb_stride, int64_t n,
+                        float* x, cudaStream_t st, const DevInfo& di, int64_t cap, const SolveLayout& Lo,
+                        int32_t* launches) {
   char* base = (char*)p->solve_buf;
-  cudaStream_t st = (cudaStream_t)stream;
-  int32_t launches = 0;
-  const size_t es = elem_size(p->rule);
-  cudaError_t e = cudaMemsetAsync(base + Lo.ya, 0, Lo.part - Lo.ya, st);  // Y_A and Y_b
-  if (e != cudaSuccess) return cuda_fail(e, "zeroing sketches");
-  e = cudaMemsetAsync(base + Lo.status, 0, 4, st);
-  if (e != cudaSuccess) return cuda_fail(e, "zeroing status");
-  (void)es;
-  int64_t R_used = 0;
-  s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, base + Lo.ya, 0, st, &launches, &R_used);
-  if (s != SK_OK) return s;
-  // Sb is column n of [A | b]: the same chunks, and the rounding bits of global column n.
-  s = enqueue_sketch(p, b, 1, 1, p->row_offset, p->m, base + Lo.yb, R_used, st, &launches, nullptr, n);
-  if (s != SK_OK) return s;
   SolveLaunch L;
   L.wait_cycles = p->solve_wait_cycles;
-  L.SA = base + Lo.ya;
-  L.Sb = base + Lo.yb;
-  L.lda_sa = n;
-  L.sb_stride = 1;
+  L.SA = SA;
+  L.Sb = Sb;
+  L.lda_sa = lda_sa;
+  L.sb_stride = sb_stride;
   L.rule = p->rule;
   L.src_fp64 = 0;
   L.n = n;
@@ -935,7 +904,7 @@ sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const floa
       G.solve_x = 0;
       G.ncta = solve_ctas(G.d, n, di.sms, (size_t)di.optin);
       if (G.ncta < 1) return set_error(SK_ERR_UNSUPPORTED, "QR group of %lld rows does not fit", (long long)G.d);
-      e = launch_solve(G, st, &launches);
+      cudaError_t e = launch_solve(G, st, launches);
       if (e != cudaSuccess) return cuda_fail(e, "QR group launch");
     }
     L.SA = dst;
@@ -951,10 +920,98 @@ sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const floa
   L.solve_x = 1;
   L.ncta = solve_ctas(rows, n, di.sms, (size_t)di.optin);
   if (L.ncta < 1) return set_error(SK_ERR_UNSUPPORTED, "FP64 QR of a %lld x %lld matrix does not fit", (long long)rows, (long long)(n + 1));
-  e = launch_solve(L, st, &launches);
+  cudaError_t e = launch_solve(L, st, launches);
   if (e != cudaSuccess) return cuda_fail(e, "QR launch");
+  return SK_OK;
+}
+
+}  // namespace
+
+sk_status sk_solve(sk_plan p, const float* A, int64_t lda, int64_t n, const float* b, float* x, void* stream) {
+  clear_error();
+  sk_status s = validate_apply(p, A, lda, n, x);
+  if (s != SK_OK) return s;
+  if (!b) return set_error(SK_ERR_INVALID_ARG, "b is NULL");
+  if (n > p->d) return set_error(SK_ERR_INVALID_ARG, "sketch-and-solve needs n=%lld <= d=%lld", (long long)n, (long long)p->d);
+  if (n > kMaxSolveN) return set_error(SK_ERR_UNSUPPORTED, "sketch-and-solve supports n <= %d", kMaxSolveN);
+  DevInfo di;
+  s = dev_info(&di);
+  if (s != SK_OK) return s;
+  const int64_t cap = solve_group_cap(p, n, di);
+  if (cap < 1)
+    return set_error(SK_ERR_UNSUPPORTED, "FP64 QR of a %lld x %lld sketch: too many columns for shared memory",
+                     (long long)p->d, (long long)(n + 1));
+  const int64_t groups1 = (p->d > cap) ? (p->d + cap - 1) / cap : 0;
+  const SolveLayout Lo = solve_layout(p->d, n, p->rule, groups1);
+  if (p->solve_bytes < Lo.total) {
+    s = plan_grow(p, &p->solve_buf, &p->solve_bytes, Lo.total, "sketch-and-solve scratch");
+    if (s != SK_OK) return s;
+    // On the call's stream: a memset on the legacy default stream is not ordered with a non-blocking
+    // caller stream and could land after this call's kernels have written the scratch.
+    cudaError_t ez = cudaMemsetAsync(p->solve_buf, 0, Lo.total, (cudaStream_t)stream);
+    if (ez != cudaSuccess) return cuda_fail(ez, "zeroing sketch-and-solve scratch");
+  }
+  p->solve_status_off = Lo.status;
+  p->solve_kappa_off = Lo.kappa;
+  char* base = (char*)p->solve_buf;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t launches = 0;
+  const size_t es = elem_size(p->rule);
+  cudaError_t e = cudaMemsetAsync(base + Lo.ya, 0, Lo.part - Lo.ya, st);  // Y_A and Y_b
+  if (e != cudaSuccess) return cuda_fail(e, "zeroing sketches");
+  e = cudaMemsetAsync(base + Lo.status, 0, 4, st);
+  if (e != cudaSuccess) return cuda_fail(e, "zeroing status");
+  (void)es;
+  int64_t R_used = 0;
+  s = enqueue_sketch(p, A, lda, n, p->row_offset, p->m, base + Lo.ya, 0, st, &launches, &R_used);
+  if (s != SK_OK) return s;
+  // Sb is column n of [A | b]: the same chunks, and the rounding bits of global column n.
+  s = enqueue_sketch(p, b, 1, 1, p->row_offset, p->m, base + Lo.yb, R_used, st, &launches, nullptr, n);
+  if (s != SK_OK) return s;
+  s = solve_backend(p, base + Lo.ya, n, base + Lo.yb, 1, n, x, st, di, cap, Lo, &launches);
+  if (s != SK_OK) return s;
   p->last_launches = launches;
   p->last_R = R_used;
+  return SK_OK;
+}
+
+sk_status sk_solve_sketched(sk_plan p, const void* SAb, int64_t ld, int64_t n, float* x, void* stream) {
+  clear_error();
+  if (!p) return set_error(SK_ERR_INVALID_ARG, "plan is NULL");
+  if (!SAb || !x) return set_error(SK_ERR_INVALID_ARG, "NULL sketch or x");
+  if (n < 1 || ld < n + 1) return set_error(SK_ERR_INVALID_ARG, "need n >= 1 and ld >= n + 1 (n=%lld ld=%lld)",
+                                            (long long)n, (long long)ld);
+  if (n > p->d) return set_error(SK_ERR_INVALID_ARG, "sketch-and-solve needs n=%lld <= d=%lld", (long long)n, (long long)p->d);
+  if (n > kMaxSolveN) return set_error(SK_ERR_UNSUPPORTED, "sketch-and-solve supports n <= %d", kMaxSolveN);
+  const size_t es = elem_size(p->rule);
+  if ((reinterpret_cast<uintptr_t>(SAb) % es) != 0) return set_error(SK_ERR_INVALID_ARG, "sketch not aligned to its elements");
+  DevInfo di;
+  sk_status s = dev_info(&di);
+  if (s != SK_OK) return s;
+  const int64_t cap = solve_group_cap(p, n, di);
+  if (cap < 1)
+    return set_error(SK_ERR_UNSUPPORTED, "FP64 QR of a %lld x %lld sketch: too many columns for shared memory",
+                     (long long)p->d, (long long)(n + 1));
+  const int64_t groups1 = (p->d > cap) ? (p->d + cap - 1) / cap : 0;
+  const SolveLayout Lo = solve_layout(p->d, n, p->rule, groups1);
+  if (p->solve_bytes < Lo.total) {
+    s = plan_grow(p, &p->solve_buf, &p->solve_bytes, Lo.total, "sketch-and-solve scratch");
+    if (s != SK_OK) return s;
+    // On the call's stream: a memset on the legacy default stream is not ordered with a non-blocking
+    // caller stream and could land after this call's kernels have written the scratch.
+    cudaError_t ez = cudaMemsetAsync(p->solve_buf, 0, Lo.total, (cudaStream_t)stream);
+    if (ez != cudaSuccess) return cuda_fail(ez, "zeroing sketch-and-solve scratch");
+  }
+  p->solve_status_off = Lo.status;
+  p->solve_kappa_off = Lo.kappa;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync((char*)p->solve_buf + Lo.status, 0, 4, st);
+  if (e != cudaSuccess) return cuda_fail(e, "zeroing status");
+  int32_t launches = 0;
+  const char* sa = static_cast<const char*>(SAb);
+  s = solve_backend(p, sa, ld, sa + es * (size_t)n, ld, n, x, st, di, cap, Lo, &launches);
+  if (s != SK_OK) return s;
+  p->last_launches = launches;
   return SK_OK;
 }
 

@@ -134,6 +134,7 @@ struct sk_batch_s {
   int32_t rule = 0;
   int32_t threads = 0, tile_cols = 0;
   int64_t chunk_rows = 0;
+  int64_t item_chunks = 0;  // > 0: each item's chunk length from its own m (SK_PARAM_ITEM_CHUNKS)
   bool built = false;
   int device = 0;
   // device state
@@ -150,6 +151,13 @@ struct sk_batch_s {
   int64_t bytes_A = 0;
   size_t smem = 0;
   int32_t grid = 0, use_threads = 0;
+  // Device buffers are grown, never shrunk, so a batch rebound to new items reuses them; the host
+  // copies of the uploaded tables stay alive until the asynchronous uploads have run.
+  size_t cap_maps = 0, cap_descs = 0, cap_work = 0, cap_zero = 0;
+  std::vector<CUtensorMap> h_maps;
+  std::vector<BatchDesc> h_descs;
+  std::vector<BatchWork> h_work;
+  std::vector<ZeroSpan> h_zero;
 };
 
 namespace {
@@ -167,10 +175,49 @@ void free_batch_dev(sk_batch_s* b) {
   b->d_work = nullptr;
   b->d_zero = nullptr;
   b->d_counter = nullptr;
+  b->cap_maps = b->cap_descs = b->cap_work = b->cap_zero = 0;
 }
 
-// Build the work list and upload it (called on the first launch so that overrides apply).
-sk_status build_batch(sk_batch_s* b) {
+// Device array of at least `count` elements of T in *ptr (capacity *cap, in elements): kept if large
+// enough, else replaced (grown to 1.5x, so a batch rebound to slowly growing item lists reallocates
+// rarely).
+template <typename T>
+bool ensure_dev(T** ptr, size_t* cap, size_t count) {
+  count = std::max<size_t>(count, 1);
+  if (*ptr && *cap >= count) return true;
+  const size_t want = std::max(count, *cap + *cap / 2);
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  if (cudaMalloc(reinterpret_cast<void**>(ptr), sizeof(T) * want) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return false;
+  }
+  *cap = want;
+  return true;
+}
+
+// Validate batch items (the checks of sk_batch_create and sk_batch_rebind).
+sk_status validate_items(const sk_batch_item* items, int32_t count) {
+  if (!items || count < 1) return set_error(SK_ERR_INVALID_ARG, "need at least one item");
+  for (int32_t i = 0; i < count; ++i) {
+    const sk_batch_item& it = items[i];
+    if (!it.A_dev || !it.Y_dev) return set_error(SK_ERR_INVALID_ARG, "item %d: NULL pointer", i);
+    if (it.m < 1 || it.n < 1 || it.n > 65535 || it.lda < it.n || it.d < 1 || it.k < 1 || it.k > 64 ||
+        it.d % it.k != 0)
+      return set_error(SK_ERR_INVALID_ARG, "item %d: invalid sizes (m=%lld n=%lld lda=%lld d=%lld k=%d)", i,
+                       (long long)it.m, (long long)it.n, (long long)it.lda, (long long)it.d, it.k);
+    if ((reinterpret_cast<uintptr_t>(it.Y_dev) & 3u) != 0)
+      return set_error(SK_ERR_INVALID_ARG, "item %d: Y must be 4-byte aligned", i);
+    if (it.d / it.k > 0x7fffffffLL) return set_error(SK_ERR_UNSUPPORTED, "item %d: block too large", i);
+  }
+  return SK_OK;
+}
+
+// Build the work list and upload it on `st` (called on the first launch after a create or a rebind,
+// so that overrides apply).
+sk_status build_batch(sk_batch_s* b, cudaStream_t st) {
   int dev = 0, sms = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return set_error(SK_ERR_CUDA, "cudaGetDevice failed");
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -261,6 +308,9 @@ sk_status build_batch(sk_batch_s* b) {
     int64_t R;
     if (b->chunk_rows > 0) {
       R = b->chunk_rows;
+    } else if (b->item_chunks > 0) {
+      R = std::max<int64_t>(4096, (it.m + b->item_chunks - 1) / b->item_chunks);
+      R = ((R + 255) / 256) * 256;
     } else {
       const double per_row = (double)ncgs[i] * NC * it.k;
       R = (int64_t)std::ceil(target_cost / std::max(per_row, 1.0));
@@ -291,15 +341,16 @@ sk_status build_batch(sk_batch_s* b) {
     const double cy = (double)(y.r1 - y.r0) * y.kbe * (1 << descs[y.item].D.log2NC);
     return cx > cy;
   });
-  std::vector<ZeroSpan> zs(count);
+  std::vector<ZeroSpan>& zs = b->h_zero;
+  zs.assign(count, ZeroSpan());
   for (int32_t i = 0; i < count; ++i) {
     const int64_t es = (b->rule == SK_FP32) ? 4 : 2;
     zs[i].p = b->items[i].Y_dev;
     zs[i].bytes = b->items[i].d * b->items[i].n * es;
   }
-  free_batch_dev(b);
   // One tensor map per item (A staged through TMA where its layout allows it).
-  std::vector<CUtensorMap> maps(count);
+  std::vector<CUtensorMap>& maps = b->h_maps;
+  maps.assign(count, CUtensorMap());
   std::vector<int> has_map(count, 0);
   for (int32_t i = 0; i < count; ++i) {
     memset(&maps[i], 0, sizeof(CUtensorMap));
@@ -314,28 +365,30 @@ sk_status build_batch(sk_batch_s* b) {
       descs[i].D.lr = 0;
     }
   }
-  if (cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * count) != cudaSuccess ||
-      cudaMalloc(&b->d_status, sizeof(unsigned)) != cudaSuccess) {
-    free_batch_dev(b);
-    cudaGetLastError();
-    return set_error(SK_ERR_OOM, "batch tensor map allocation failed");
+  if (!b->d_status) {
+    if (cudaMalloc(&b->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->d_counter, sizeof(int32_t)) != cudaSuccess) {
+      free_batch_dev(b);
+      cudaGetLastError();
+      return set_error(SK_ERR_OOM, "batch status allocation failed");
+    }
   }
-  cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * count, cudaMemcpyHostToDevice);
-  cudaMemset(b->d_status, 0, sizeof(unsigned));
-  for (int32_t i = 0; i < count; ++i) descs[i].D.tmap = has_map[i] ? (const void*)(b->d_maps + i) : nullptr;
-  if (cudaMalloc(&b->d_descs, sizeof(BatchDesc) * count) != cudaSuccess ||
-      cudaMalloc(&b->d_work, sizeof(BatchWork) * std::max<size_t>(work.size(), 1)) != cudaSuccess ||
-      cudaMalloc(&b->d_zero, sizeof(ZeroSpan) * count) != cudaSuccess ||
-      cudaMalloc(&b->d_counter, sizeof(int32_t)) != cudaSuccess) {
+  cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st);
+  if (!ensure_dev(&b->d_maps, &b->cap_maps, (size_t)count) || !ensure_dev(&b->d_descs, &b->cap_descs, (size_t)count) ||
+      !ensure_dev(&b->d_work, &b->cap_work, work.size()) || !ensure_dev(&b->d_zero, &b->cap_zero, (size_t)count)) {
     free_batch_dev(b);
-    cudaGetLastError();
     return set_error(SK_ERR_OOM, "batch work list allocation failed");
   }
-  cudaMemcpy(b->d_descs, descs.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice);
-  if (!work.empty()) cudaMemcpy(b->d_work, work.data(), sizeof(BatchWork) * work.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(b->d_zero, zs.data(), sizeof(ZeroSpan) * count, cudaMemcpyHostToDevice);
-  cudaMemset(b->d_counter, 0, sizeof(int32_t));
-  b->nwork = (int64_t)work.size();
+  for (int32_t i = 0; i < count; ++i) descs[i].D.tmap = has_map[i] ? (const void*)(b->d_maps + i) : nullptr;
+  b->h_descs.swap(descs);
+  b->h_work.swap(work);
+  cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * count, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b->d_descs, b->h_descs.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st);
+  if (!b->h_work.empty())
+    cudaMemcpyAsync(b->d_work, b->h_work.data(), sizeof(BatchWork) * b->h_work.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b->d_zero, zs.data(), sizeof(ZeroSpan) * count, cudaMemcpyHostToDevice, st);
+  b->nwork = (int64_t)b->h_work.size();
   b->acc_floats = (int64_t)max_floats;
   b->slot_bytes = slot_max;
   {
@@ -369,24 +422,24 @@ sk_status sk_batch_create(const sk_batch_item* items, int32_t count, int32_t rul
   clear_error();
   if (!out) return set_error(SK_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (!items || count < 1) return set_error(SK_ERR_INVALID_ARG, "need at least one item");
   if (rule < SK_FP32 || rule > SK_BF16_RN) return set_error(SK_ERR_INVALID_ARG, "unknown rule %d", rule);
-  for (int32_t i = 0; i < count; ++i) {
-    const sk_batch_item& it = items[i];
-    if (!it.A_dev || !it.Y_dev) return set_error(SK_ERR_INVALID_ARG, "item %d: NULL pointer", i);
-    if (it.m < 1 || it.n < 1 || it.n > 65535 || it.lda < it.n || it.d < 1 || it.k < 1 || it.k > 64 ||
-        it.d % it.k != 0)
-      return set_error(SK_ERR_INVALID_ARG, "item %d: invalid sizes (m=%lld n=%lld lda=%lld d=%lld k=%d)", i,
-                       (long long)it.m, (long long)it.n, (long long)it.lda, (long long)it.d, it.k);
-    if ((reinterpret_cast<uintptr_t>(it.Y_dev) & 3u) != 0)
-      return set_error(SK_ERR_INVALID_ARG, "item %d: Y must be 4-byte aligned", i);
-    if (it.d / it.k > 0x7fffffffLL) return set_error(SK_ERR_UNSUPPORTED, "item %d: block too large", i);
-  }
+  sk_status s = validate_items(items, count);
+  if (s != SK_OK) return s;
   sk_batch_s* b = new (std::nothrow) sk_batch_s();
   if (!b) return set_error(SK_ERR_OOM, "host allocation failed");
   b->items.assign(items, items + count);
   b->rule = rule;
   *out = b;
+  return SK_OK;
+}
+
+sk_status sk_batch_rebind(sk_batch b, const sk_batch_item* items, int32_t count) {
+  clear_error();
+  if (!b) return set_error(SK_ERR_INVALID_ARG, "batch is NULL");
+  sk_status s = validate_items(items, count);
+  if (s != SK_OK) return s;
+  b->items.assign(items, items + count);
+  b->built = false;
   return SK_OK;
 }
 
@@ -409,6 +462,10 @@ sk_status sk_batch_set(sk_batch b, int32_t key, int64_t value) {
       if (value < 0) return set_error(SK_ERR_INVALID_ARG, "chunk rows must be >= 0");
       b->chunk_rows = value;
       return SK_OK;
+    case SK_PARAM_ITEM_CHUNKS:
+      if (value < 0) return set_error(SK_ERR_INVALID_ARG, "chunks per item must be >= 0");
+      b->item_chunks = value;
+      return SK_OK;
     default:
       return set_error(SK_ERR_INVALID_ARG, "unknown batch key %d", key);
   }
@@ -418,7 +475,7 @@ sk_status sk_batch_launch(sk_batch b, void* stream) {
   clear_error();
   if (!b) return set_error(SK_ERR_INVALID_ARG, "batch is NULL");
   if (!b->built) {
-    sk_status s = build_batch(b);
+    sk_status s = build_batch(b, (cudaStream_t)stream);
     if (s != SK_OK) return s;
   }
   int32_t launches = 0;
@@ -433,7 +490,7 @@ sk_status sk_batch_info(sk_batch b, int64_t* work_items, int64_t* bytes_A) {
   clear_error();
   if (!b) return set_error(SK_ERR_INVALID_ARG, "batch is NULL");
   if (!b->built) {
-    sk_status s = build_batch(b);
+    sk_status s = build_batch(b, 0);
     if (s != SK_OK) return s;
   }
   if (work_items) *work_items = b->nwork;

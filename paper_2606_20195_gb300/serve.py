@@ -1,19 +1,26 @@
 """Continuous-batching server for sketch-and-solve least-squares requests (libsk C ABI).
 
-Requests arrive over time (a Poisson stream in the benchmark). The server keeps a fixed number of
-slots, each a CUDA stream, and an HBM budget. A waiting request is admitted as soon as a slot is free
-and its device footprint fits the budget; admitted requests run concurrently on their streams, so
-requests that arrive while others are on the GPU overlap with them. Plans (and the device scratch
-they own: sketches, FP64 QR workspace, chunk buffers) are cached per (d, k, rule) and reused by later
-requests of any height (SK_PARAM_ROWS sets a request's m on the cached plan), so once the scratch has
-grown to the largest request seen, serving allocates no device memory: a cudaMalloc in the middle of
-the stream would synchronize every slot's stream. Latency is measured from arrival to the moment x is
-ready.
+Requests arrive over time (a Poisson stream in the benchmark). The server keeps a slot count (the
+most requests on the GPU at once), a pool of CUDA streams and an HBM budget. A waiting request is
+admitted as soon as a slot is free and its device footprint fits the budget. At every scheduling
+step the requests admitted in that step are batched: for each rounding rule among them, ONE batched
+sketch launch (sk_batch_launch, a persistent kernel over a device work list) forms S [A_i | b_i] for
+all of them, then each request's FP64 QR and triangular solve run from its sketch
+(sk_solve_sketched), on the same stream. Requests admitted while earlier ones are still on the GPU
+run on other streams and overlap with them. Plans (which own the FP64 QR workspace) are cached per
+(d, k, rule), and batch objects per rule are rebound to the next step's requests once their last
+launch has completed (sk_batch_rebind), so once the pools have warmed up serving allocates no device
+memory: a cudaMalloc or cudaFree in the middle of the stream would synchronize every stream.
+Latency is measured from arrival to the moment x is ready.
+
+With deterministic=True the server runs each request through sk_solve in SK_MODE_DETERMINISTIC
+instead (the batched kernel runs in atomic mode only), so that results can be compared bit for bit
+alone and in the mix.
 
 Device memory for requests comes from one arena: a buffer the size of the HBM budget, allocated when
-the server starts, in which every admitted request's A, b and x get a range (first fit, freed when
-the request completes). Admission needs both a free slot and a range; serving itself never calls the
-CUDA allocator, whose cudaMalloc / cudaFree of multi-GB blocks would synchronize every slot's stream.
+the server starts, in which every admitted request's [A | b] (A and b side by side, row stride
+n + 1 rounded up to 4 floats, the layout the batched TMA staging reads), its sketch and x get a range
+(first fit, freed when the request completes). Admission needs both a free slot and a range.
 
 Each request's matrix is materialized on the device by a seeded generator when it is admitted
 (synthetic workloads; the same families the tests and benchmarks use). That generation stands in for
@@ -49,6 +56,7 @@ class Request:
     admitted: float = math.nan
     done: float = math.nan
     x: object = None
+    sketch: object = None         # [SA | Sb] on the host (keep_sketches)
     status: int = -1
     kappa: float = math.nan
 
@@ -57,9 +65,19 @@ class Request:
         return self.done - self.arrival
 
 
+def ab_stride(n: int) -> int:
+    """Row stride (floats) of a request's [A | b]: n + 1 rounded up to a multiple of 4 (16 bytes)."""
+    return (n + 1 + 3) // 4 * 4
+
+
+def sketch_elem_bytes(rule: int) -> int:
+    return 4 if rule == skb.SK_FP32 else 2
+
+
 def footprint_bytes(req: Request) -> int:
-    """Device bytes a request holds while admitted: A, b and x."""
-    return req.m * req.n * 4 + req.m * 4 + req.n * 4
+    """Device bytes a request holds while admitted: [A | b], its sketch, x and x*."""
+    return (req.m * ab_stride(req.n) * 4 + req.d * (req.n + 1) * sketch_elem_bytes(req.rule)
+            + 2 * req.n * 4)
 
 
 def plan_scratch_bytes(req: Request) -> int:
@@ -144,7 +162,7 @@ class Arena:
 
 class Server:
     def __init__(self, slots: int = 8, hbm_budget_bytes: int = 120 * 10**9, device: str = "cuda:0",
-                 deterministic: bool = False, keep_results: bool = True):
+                 deterministic: bool = False, keep_results: bool = True, keep_sketches: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -157,6 +175,10 @@ class Server:
         self.resident_bytes = 0      # device scratch kept by cached plans
         self.deterministic = deterministic
         self.keep_results = keep_results
+        self.keep_sketches = keep_sketches  # copy each request's sketch [SA | Sb] to the host (tests)
+        self.batches: dict = {}      # rule -> list of [batch handle, event of its last launch or None]
+        self.launches = 0            # batched sketch launches made (one per rule and scheduling step)
+        self._rr = 0                 # next stream of the pool
         self.peak_bytes = 0
         self.arena = Arena(self.budget // 4, self.device)
 
@@ -170,13 +192,31 @@ class Server:
                 entry[0].set(skb.SK_PARAM_ROWS, req.m)
                 return entry[0], (key, idx)
         mode = skb.SK_MODE_DETERMINISTIC if self.deterministic else skb.SK_MODE_ATOMIC
-        # The sketch seed is derived from (d, k, rule), so a cached plan serves every request of them.
-        seed = (req.d * 1000003 + req.k * 13 + req.rule) & 0xFFFFFFFF
-        plan = skb.Plan(req.d, req.m, req.k, req.rule, seed=seed, mode=mode)
+        plan = skb.Plan(req.d, req.m, req.k, req.rule, seed=self.sketch_seed(req), mode=mode)
         est = plan_scratch_bytes(req)
         pool.append([plan, True, est])
         self.resident_bytes += est
         return plan, (key, len(pool) - 1)
+
+    @staticmethod
+    def sketch_seed(req: Request) -> int:
+        """The sketch seed is derived from (d, k, rule), so a cached plan serves every request of them."""
+        return (req.d * 1000003 + req.k * 13 + req.rule) & 0xFFFFFFFF
+
+    def _batch(self, rule: int, items: list):
+        """A batch object of this rule whose last launch has completed, bound to `items`."""
+        pool = self.batches.setdefault(rule, [])
+        for entry in pool:
+            if entry[1] is None or entry[1].query():
+                skb.sk_batch_rebind(entry[0], items)
+                break
+        else:
+            entry = [skb.sk_batch_create(items, rule), None]
+            pool.append(entry)
+        # Each request's chunking from its own m (at most 8 chunks, as sk_solve's default), so its
+        # rounding does not depend on the other requests of the step.
+        skb.sk_batch_set(entry[0], skb.SK_PARAM_ITEM_CHUNKS, 8)
+        return entry
 
     def _release_plan(self, key):
         entry = self.plans[key[0]][key[1]]
@@ -192,10 +232,11 @@ class Server:
         return Arena.ALIGN * ((n + Arena.ALIGN - 1) // Arena.ALIGN)
 
     def _place(self, req: Request):
-        """Arena ranges for A (m x n), b (m) and x followed by x* (each at an aligned start); None if
-        they do not all fit."""
+        """Arena ranges for [A | b] (m x ab_stride(n)), the sketch (d x (n+1) elements of the rule's
+        type) and x followed by x*; None if they do not all fit."""
         got = []
-        for numel in (req.m * req.n, req.m, self._xs_offset(req.n) + req.n):
+        sk_floats = (req.d * (req.n + 1) * sketch_elem_bytes(req.rule) + 3) // 4
+        for numel in (req.m * ab_stride(req.n), sk_floats, self._xs_offset(req.n) + req.n):
             o = self.arena.alloc(numel)
             if o is None:
                 for o2, n2 in got:
@@ -204,34 +245,100 @@ class Server:
             got.append((o, numel))
         return got
 
-    def _launch(self, req: Request, slot: int, ranges):
-        torch = self.torch
-        st = self.streams[slot]
-        (oa, _), (ob, _), (ox, _) = ranges
-        A = self.arena.view(oa, (req.m, req.n))
-        b = self.arena.view(ob, (req.m,))
+    def _views(self, req: Request, ranges):
+        (oa, _), (oy, _), (ox, _) = ranges
+        Ab = self.arena.view(oa, (req.m, ab_stride(req.n)))
         x = self.arena.view(ox, (req.n,))
         xs = self.arena.view(ox + self._xs_offset(req.n), (req.n,))
+        return Ab, Ab[:, :req.n], Ab[:, req.n], x, xs, oy
+
+    def _generate(self, req: Request, A, b, xs):
+        """The request's data (on the current stream): A of its family, x* ~ N(0,1) and
+        b = A x* + 1e-6 N(0,1)."""
+        torch = self.torch
+        inputs.fill_device_matrix(A, req.family, seed=req.seed)
+        g = torch.Generator(device=self.device)
+        g.manual_seed(req.seed + 7)
+        torch.randn(req.n, generator=g, out=xs)
+        torch.randn(req.m, generator=g, out=b)
+        b.mul_(1e-6).addmv_(A, xs)
+
+    def problem(self, req: Request):
+        """(A, b) of a request as numpy arrays, generated exactly as the server generates them (in
+        the same [A | b] layout), for checking served results."""
+        torch = self.torch
+        Ab = torch.empty((req.m, ab_stride(req.n)), dtype=torch.float32, device=self.device)
+        xs = torch.empty(req.n, dtype=torch.float32, device=self.device)
+        self._generate(req, Ab[:, :req.n], Ab[:, req.n], xs)
+        torch.cuda.synchronize(self.device)
+        return Ab[:, :req.n].cpu().numpy(), Ab[:, req.n].cpu().numpy()
+
+    def _next_stream(self):
+        st = self.streams[self._rr % len(self.streams)]
+        self._rr += 1
+        return st
+
+    def _launch_group(self, admitted: list):
+        """Jobs for the requests admitted in one scheduling step: per rule, their data, one batched
+        sketch launch over all their [A | b], then each one's QR solve from its sketch."""
+        torch = self.torch
+        by_rule: dict = {}
+        for req, slot, ranges in admitted:
+            by_rule.setdefault(req.rule, []).append((req, slot, ranges))
+        jobs = []
+        for rule, group in by_rule.items():
+            st = self._next_stream()
+            with torch.cuda.stream(st):
+                items = []
+                for req, slot, ranges in group:
+                    Ab, A, b, x, xs, oy = self._views(req, ranges)
+                    self._generate(req, A, b, xs)
+                    items.append({"A": Ab, "Y": self.arena.buf[oy:], "m": req.m, "n": req.n + 1,
+                                  "lda": ab_stride(req.n), "d": req.d, "k": req.k, "seed": self.sketch_seed(req)})
+                entry = self._batch(rule, items)
+                skb.sk_batch_launch(entry[0], st)
+                self.launches += 1
+                for (req, slot, ranges), it in zip(group, items):
+                    _, _, _, x, _, _ = self._views(req, ranges)
+                    plan, key = self._plan(req)
+                    skb.sk_solve_sketched(plan.handle, it["Y"], req.n + 1, req.n, x, st)
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                    jobs.append({"req": req, "slot": slot, "ranges": ranges, "x": x, "plan": plan, "key": key,
+                                 "event": ev, "stream": st, "sketch": it["Y"]})
+                entry[1] = jobs[-1]["event"]  # the batch is free again once its group's last solve is done
+        return jobs
+
+    def _launch_single(self, req: Request, slot: int, ranges):
+        """One request on its own (the one-at-a-time baseline and the deterministic mode): the plan's
+        sketch of [A | b] (sk_apply over the n + 1 columns: column n is S b with the rounding bits of
+        column n, as sk_solve forms it), then the FP64 back end (sk_solve_sketched)."""
+        torch = self.torch
+        st = self.streams[slot % len(self.streams)]
+        Ab, A, b, x, xs, oy = self._views(req, ranges)
+        Y = self.arena.buf[oy:]
         with torch.cuda.stream(st):
-            inputs.fill_device_matrix(A, req.family, seed=req.seed)
-            g = torch.Generator(device=self.device)
-            g.manual_seed(req.seed + 7)
-            torch.randn(req.n, generator=g, out=xs)
-            torch.randn(req.m, generator=g, out=b)
-            b.mul_(1e-6).addmv_(A, xs)  # b = A x* + 1e-6 N(0, 1)
+            self._generate(req, A, b, xs)
             plan, key = self._plan(req)
-            skb.sk_solve(plan.handle, A, req.n, req.n, b, x, st)
+            skb.sk_apply(plan.handle, Ab, ab_stride(req.n), req.n + 1, Y, st)
+            skb.sk_solve_sketched(plan.handle, Y, req.n + 1, req.n, x, st)
             ev = torch.cuda.Event()
             ev.record(st)
-        return {"req": req, "slot": slot, "ranges": ranges, "x": x, "plan": plan, "key": key, "event": ev}
+        return {"req": req, "slot": slot, "ranges": ranges, "x": x, "plan": plan, "key": key, "event": ev,
+                "stream": st, "sketch": Y}
 
     def _finish(self, job, now: float):
         req = job["req"]
         req.done = now
-        status, kappa = job["plan"].solve_status(self.streams[job["slot"]])
+        status, kappa = job["plan"].solve_status(job["stream"])
         req.status, req.kappa = status, kappa
         if self.keep_results:
             req.x = job["x"].cpu()
+        if self.keep_sketches and job["sketch"] is not None:
+            es = sketch_elem_bytes(req.rule)
+            raw = job["sketch"][:(req.d * (req.n + 1) * es + 3) // 4].cpu().numpy().view(np.uint8)
+            dt = np.float32 if es == 4 else np.uint16
+            req.sketch = raw[:req.d * (req.n + 1) * es].view(dt).reshape(req.d, req.n + 1).copy()
         for o, numel in job["ranges"]:
             self.arena.release(o, numel)
         self._release_plan(job["key"])
@@ -264,7 +371,9 @@ class Server:
                 else:
                     still.append(job)
             running = still
-            # admissions (FIFO by arrival; a request that does not fit waits for memory)
+            # admissions (FIFO by arrival; a request that does not fit waits for memory), then the
+            # step's admitted requests are launched together
+            admitted = []
             while waiting and self.free_slots:
                 req = waiting[0][2]
                 fb = footprint_bytes(req)
@@ -282,7 +391,12 @@ class Server:
                 self.used_bytes += fb
                 self.peak_bytes = max(self.peak_bytes, self.used_bytes + self.resident_bytes)
                 req.admitted = clock() - t0
-                running.append(self._launch(req, slot, ranges))
+                if self.deterministic:
+                    running.append(self._launch_single(req, slot, ranges))
+                else:
+                    admitted.append((req, slot, ranges))
+            if admitted:
+                running.extend(self._launch_group(admitted))
             if not running and not waiting and i < len(pending):
                 # idle until the next arrival
                 delay = pending[i].arrival - (clock() - t0)
@@ -306,7 +420,7 @@ class Server:
             ranges = self._place(req)
             if ranges is None:
                 raise ValueError(f"request {req.rid} does not fit in the arena")
-            job = self._launch(req, self.free_slots.pop(0), ranges)
+            job = self._launch_single(req, self.free_slots.pop(0), ranges)
             job["event"].synchronize()
             self._finish(job, clock() - t0)
         return summarize(requests, clock() - t0)
@@ -329,6 +443,10 @@ class Server:
             for entry in pool:
                 entry[0].close()
         self.plans.clear()
+        for pool in self.batches.values():
+            for entry in pool:
+                skb.sk_batch_destroy(entry[0])
+        self.batches.clear()
         self.resident_bytes = 0
         self.arena = None
 

@@ -20,6 +20,7 @@ SK_PARAM_CHUNK_ROWS, SK_PARAM_MODE, SK_PARAM_ROW_OFFSET, SK_PARAM_KERNEL = 1, 2,
 SK_PARAM_TILE_COLS, SK_PARAM_THREADS, SK_PARAM_LAST_LAUNCHES, SK_PARAM_LAST_CHUNK_ROWS = 5, 6, 7, 8
 SK_PARAM_DEVICE_STATUS, SK_PARAM_LAST_KERNEL, SK_PARAM_SOLVE_GROUP_ROWS, SK_PARAM_LIST_CAP = 9, 10, 11, 12
 SK_PARAM_SCRATCH_LIMIT, SK_PARAM_SOLVE_WAIT_CYCLES, SK_PARAM_SCRATCH_BYTES, SK_PARAM_ROWS = 13, 14, 15, 16
+SK_PARAM_ITEM_CHUNKS = 17
 SK_MODE_ATOMIC, SK_MODE_DETERMINISTIC, SK_MODE_SERIAL_TILE = 0, 1, 2
 SK_KERNEL_AUTO, SK_KERNEL_TILE, SK_KERNEL_LITERAL, SK_KERNEL_OWNER, SK_KERNEL_GLOBAL = 0, 1, 2, 3, 4
 SK_KERNEL_REGISTER = 6
@@ -30,7 +31,8 @@ EXPORTS = [
     "sk_version", "sk_last_error", "sk_plan_create", "sk_plan_set", "sk_plan_get", "sk_apply",
     "sk_apply_host", "sk_solve", "sk_solve_status", "sk_solve_precond", "sk_materialize_S", "sk_batch_create",
     "sk_batch_set", "sk_batch_launch", "sk_batch_info", "sk_batch_destroy", "sk_destroy",
-    "sk_apply_noalloc", "sk_apply_typed", "sk_apply_partials", "sk_finish_partials",
+    "sk_apply_noalloc", "sk_apply_typed", "sk_apply_partials", "sk_finish_partials", "sk_solve_sketched",
+    "sk_batch_rebind",
 ]
 
 
@@ -87,6 +89,10 @@ def load(path: str | None = None):
     L.sk_batch_create.argtypes = [ctypes.POINTER(sk_batch_item), i32, i32, ctypes.POINTER(vp)]
     L.sk_batch_set.restype = st
     L.sk_batch_set.argtypes = [vp, i32, i64]
+    L.sk_batch_rebind.restype = st
+    L.sk_batch_rebind.argtypes = [vp, ctypes.POINTER(sk_batch_item), i32]
+    L.sk_solve_sketched.restype = st
+    L.sk_solve_sketched.argtypes = [vp, vp, i64, i64, vp, vp]
     L.sk_batch_launch.restype = st
     L.sk_batch_launch.argtypes = [vp, vp]
     L.sk_batch_info.restype = st
@@ -170,6 +176,10 @@ def sk_solve(plan: int, A, lda: int, n: int, b, x, stream=None) -> None:
     check(load().sk_solve(plan, _ptr(A), lda, n, _ptr(b), _ptr(x), _stream_handle(stream)))
 
 
+def sk_solve_sketched(plan: int, SAb, ld: int, n: int, x, stream=None) -> None:
+    check(load().sk_solve_sketched(plan, _ptr(SAb), ld, n, _ptr(x), _stream_handle(stream)))
+
+
 def sk_solve_status(plan: int, stream=None) -> tuple[int, float]:
     kap = ctypes.c_double()
     s = load().sk_solve_status(plan, ctypes.byref(kap), _stream_handle(stream))
@@ -189,7 +199,7 @@ def sk_materialize_S(plan: int, i0: int, cnt: int, rows, signs, stream=None) -> 
     check(load().sk_materialize_S(plan, i0, cnt, _ptr(rows), _ptr(signs), _stream_handle(stream)))
 
 
-def sk_batch_create(items: list[dict], rule: int) -> int:
+def _batch_items(items: list[dict]):
     arr = (sk_batch_item * len(items))()
     for q, it in enumerate(items):
         arr[q].A_dev = _ptr(it["A"])
@@ -201,9 +211,18 @@ def sk_batch_create(items: list[dict], rule: int) -> int:
         arr[q].k = it["k"]
         arr[q].pad_ = 0
         arr[q].seed = it.get("seed", 0) & (2**64 - 1)
+    return arr
+
+
+def sk_batch_create(items: list[dict], rule: int) -> int:
+    arr = _batch_items(items)
     out = ctypes.c_void_p()
     check(load().sk_batch_create(arr, len(items), rule, ctypes.byref(out)))
     return out.value
+
+
+def sk_batch_rebind(batch: int, items: list[dict]) -> None:
+    check(load().sk_batch_rebind(batch, _batch_items(items), len(items)))
 
 
 def sk_batch_set(batch: int, key: int, value: int) -> None:

@@ -17,21 +17,114 @@ def _stream(count, seed):
 def test_results_same_alone_and_in_the_mix(sk, dev):
     from paper_2606_20195_gb300 import serve
     reqs = _stream(16, seed=3)
-    srv = serve.Server(slots=4, hbm_budget_bytes=2 * 10**9, deterministic=True)
+    srv = serve.Server(slots=4, hbm_budget_bytes=2 * 10**9, deterministic=True, keep_sketches=True)
     stats = srv.run(reqs)
     assert stats["ok"] == len(reqs)
     mixed = {r.rid: r.x.numpy().copy() for r in reqs}
+    sketches = {r.rid: r.sketch for r in reqs}
     # each request again, alone, through the one-at-a-time path
     alone = _stream(16, seed=3)
-    srv2 = serve.Server(slots=1, hbm_budget_bytes=2 * 10**9, deterministic=True)
+    srv2 = serve.Server(slots=1, hbm_budget_bytes=2 * 10**9, deterministic=True, keep_sketches=True)
     srv2.run_one_at_a_time(alone)
     for r in alone:
+        assert np.array_equal(sketches[r.rid], r.sketch), r.rid
         a, b = mixed[r.rid], r.x.numpy()
         # deterministic sketches are bit-identical; the FP64 QR reduces with atomics, so x may
         # differ in the last bits only
         assert np.allclose(a, b, rtol=1e-6, atol=1e-7), r.rid
     srv.close()
     srv2.close()
+
+
+TOL = {0: 1e-5, 1: 2e-3, 2: 2e-3, 3: 2e-3}
+
+
+def _sketch64(sk_host, rule):
+    return sk_host.astype(np.float64) if rule == 0 else oracle.halfbits_to_f64(sk_host)
+
+
+def test_batched_results_same_alone_and_in_the_mix(sk, dev):
+    # Atomic mode, batched: the requests of a scheduling step are sketched by one batched launch per
+    # rule. Each request's sketch [SA | Sb], in the mix and alone (a batch of one), is within the
+    # atomic-mode tolerance of the FP64 sketch of its [A | b] (same S), the two sketches are within
+    # that tolerance of each other, and each x is the least-squares solution of its own sketch (FP64
+    # reference on the host, to FP32 output precision). The residual ||A x - b|| itself is not
+    # compared: with b = A x* + 1e-6 noise the system is nearly consistent and the rounding of S b
+    # (FP32 or binary16) already moves it by a few percent from one atomic order to another.
+    from paper_2606_20195_gb300 import serve
+    reqs = _stream(16, seed=4)
+    for r in reqs:
+        r.arrival = 0.0  # all at once: the first step batches as many as there are slots
+    srv = serve.Server(slots=8, hbm_budget_bytes=2 * 10**9, keep_sketches=True)
+    stats = srv.run(reqs)
+    assert stats["ok"] == len(reqs)
+    assert srv.launches < len(reqs)  # some launch sketched several requests
+    alone = _stream(16, seed=4)
+    for r in alone:
+        s1 = serve.Server(slots=1, hbm_budget_bytes=2 * 10**9, keep_sketches=True)
+        s1.run([r])
+        assert r.status == sk.SK_OK and s1.launches == 1
+        s1.close()
+    for rm, ra in zip(reqs, alone):
+        A, b = srv.problem(rm)
+        ref = oracle.sketch_f64(np.column_stack([A, b]).astype(np.float32), rm.d, rm.k,
+                                serve.Server.sketch_seed(rm))
+        ym, ya = _sketch64(rm.sketch, rm.rule), _sketch64(ra.sketch, ra.rule)
+        assert oracle.rel_fro(ym, ref) <= TOL[rm.rule], rm.rid
+        assert oracle.rel_fro(ya, ref) <= TOL[rm.rule], rm.rid
+        assert oracle.rel_fro(ym, ya) <= TOL[rm.rule], rm.rid
+        for r, y in ((rm, ym), (ra, ya)):
+            xs = np.linalg.lstsq(y[:, :r.n], y[:, r.n], rcond=None)[0]
+            assert np.allclose(r.x.numpy(), xs, rtol=1e-4, atol=1e-4 * np.abs(xs).max()), r.rid
+    srv.close()
+
+
+def test_solve_sketched_matches_solve(sk, dev):
+    # sk_solve_sketched on the deterministic sketch [SA | Sb] gives the same x as sk_solve (the same
+    # FP64 back end; the QR's reductions use atomics, so the last bits may differ).
+    import torch
+    m, n, d, k = 20000, 24, 384, 4
+    A = inputs.host_matrix(m, n, "coherent", seed=3)
+    b = inputs.host_vector(m, seed=4)
+    Ad, bd = torch.from_numpy(A).to(dev), torch.from_numpy(b).to(dev)
+    for rule in (0, 1):
+        plan = sk.Plan(d, m, k, rule, 9, mode=sk.SK_MODE_DETERMINISTIC)
+        x1 = plan.solve(Ad, bd)
+        Ab = torch.from_numpy(np.column_stack([A, b]).astype(np.float32)).to(dev)
+        Y = plan.apply(Ab)  # column n: S b with the rounding bits of column n, as sk_solve forms it
+        x2 = torch.empty(n, dtype=torch.float32, device=dev)
+        sk.sk_solve_sketched(plan.handle, Y, n + 1, n, x2)
+        assert plan.solve_status()[0] == sk.SK_OK
+        assert torch.allclose(x1, x2, rtol=1e-5, atol=1e-6)
+        with pytest.raises(sk.SkError) as e:
+            sk.sk_solve_sketched(plan.handle, Y, n, n, x2)  # ld < n + 1
+        assert e.value.status == sk.SK_ERR_INVALID_ARG
+        plan.close()
+
+
+def test_batch_rebind_reuses_the_batch(sk, dev):
+    # One batch object rebound to a second, larger set of items: results within tolerance of FP64
+    # for both sets.
+    import torch
+    sets = [[(3000, 16), (5000, 32)], [(7000, 8), (2000, 64), (9000, 16)]]
+    b = None
+    for si, shapes in enumerate(sets):
+        items = []
+        for i, (mm, nn) in enumerate(shapes):
+            Ai = torch.from_numpy(inputs.host_matrix(mm, nn, "incoherent", seed=10 * si + i)).to(dev)
+            items.append({"A": Ai, "Y": torch.empty((16 * nn, nn), dtype=torch.float16, device=dev), "m": mm,
+                          "n": nn, "d": 16 * nn, "k": 4, "seed": i})
+        if b is None:
+            b = sk.sk_batch_create(items, sk.SK_FP16_RN)
+        else:
+            sk.sk_batch_rebind(b, items)
+            sk.sk_batch_set(b, sk.SK_PARAM_ITEM_CHUNKS, 2)
+        sk.sk_batch_launch(b)
+        torch.cuda.synchronize()
+        for i, it in enumerate(items):
+            ref = oracle.sketch_f64(it["A"].cpu().numpy(), it["d"], 4, i)
+            assert oracle.rel_fro(oracle.halfbits_to_f64(it["Y"].cpu().numpy().view(np.uint16)), ref) <= 2e-3
+    sk.sk_batch_destroy(b)
 
 
 def test_admission_respects_budget_and_slots(sk, dev):
@@ -56,11 +149,7 @@ def test_server_solution_quality(sk, dev):
     srv = serve.Server(slots=2, hbm_budget_bytes=10**9)
     srv.run([r])
     assert r.status == sk.SK_OK
-    A = inputs.device_matrix(r.m, r.n, r.family, seed=r.seed).cpu().numpy()
-    g = torch.Generator(device="cuda:0")
-    g.manual_seed(r.seed + 7)
-    xs = torch.randn(r.n, generator=g, device="cuda:0")
-    b = (torch.from_numpy(A).cuda() @ xs + 1e-6 * torch.randn(r.m, generator=g, device="cuda:0")).cpu().numpy()
+    A, b = srv.problem(r)
     _, r_opt = oracle.lstsq_tall(A, b)
     ratio = oracle.residual_norm(A, b, r.x.numpy().astype(np.float64)) / r_opt
     assert 1.0 <= ratio < 2.0

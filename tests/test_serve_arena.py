@@ -32,7 +32,7 @@ def test_x_and_xstar_stay_inside_their_range():
     # range must hold both, or x* would overwrite whatever the arena placed after it (another
     # request's A or b while both run).
     srv = object.__new__(serve.Server)  # placement only: no streams, no device
-    srv.arena = serve.Arena(serve.Arena.ALIGN * 1000, "cpu")
+    srv.arena = serve.Arena(serve.Arena.ALIGN * 40000, "cpu")
     for n in (1, 16, 32, 63, 64, 65, 100, 256):
         req = serve.Request(rid=0, m=128, n=n, d=16 * n, k=4, rule=0, family="incoherent", seed=0)
         ranges = srv._place(req)
