@@ -13,6 +13,25 @@
 
 namespace sk {
 
+// L2 eviction priorities: rows of A are read once (evict first), the chunk totals are reduced into
+// again and again while A streams past (evict last), so A's lines are the ones the L2 gives up.
+__device__ __forceinline__ uint64_t pol_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t pol_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ld_first(const float4* a, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
+  return v;
+}
+
 // ------------------------------------------------------------------ global-accumulator kernel
 // For blocks too tall for an on-chip accumulator (B x 4 columns of FP32 beyond shared memory): one warp
 // per input row (grid-stride over the rows). Lane j < k evaluates block j's word of the row (stream
@@ -23,6 +42,7 @@ namespace sk {
 template <typename TA, int QB>
 __global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P, int64_t row_end, int64_t R,
                                                      int64_t t_first) {
+  const uint64_t pf = pol_first(), pl = pol_last();
   const int lane = threadIdx.x & 31;
   const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -54,7 +74,7 @@ __global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P,
           if (active) {
             if (vec) {
               if constexpr (std::is_same<TA, float>::value) {
-                a = __ldg(reinterpret_cast<const float4*>(arow + col0));
+                a = ld_first(reinterpret_cast<const float4*>(arow + col0), pf);
               } else {
                 const uint2 u = __ldg(reinterpret_cast<const uint2*>(arow + col0));
                 const TA* h = reinterpret_cast<const TA*>(&u);
@@ -75,7 +95,7 @@ __global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P,
             const float x = __uint_as_float(__float_as_uint(a.x) ^ sg), y = __uint_as_float(__float_as_uint(a.y) ^ sg);
             const float z = __uint_as_float(__float_as_uint(a.z) ^ sg), w4 = __uint_as_float(__float_as_uint(a.w) ^ sg);
             if ((n & 3) == 0) {
-              asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w4)
+              asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w4), "l"(pl)
                            : "memory");
             } else {
               atomicAdd(p, x);
@@ -98,7 +118,7 @@ __global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P,
             const int64_t col0 = 4 * q;
             if (vec) {
               if constexpr (std::is_same<TA, float>::value) {
-                a[b] = __ldg(reinterpret_cast<const float4*>(arow + col0));
+                a[b] = ld_first(reinterpret_cast<const float4*>(arow + col0), pf);
               } else {
                 const uint2 u = __ldg(reinterpret_cast<const uint2*>(arow + col0));
                 const TA* h = reinterpret_cast<const TA*>(&u);
@@ -126,7 +146,7 @@ __global__ void __launch_bounds__(256) global_kernel(const TileDesc D, float* P,
               const float z = __uint_as_float(__float_as_uint(a[b].z) ^ sg);
               const float w4 = __uint_as_float(__float_as_uint(a[b].w) ^ sg);
               if ((n & 3) == 0) {
-                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w4)
+                asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w4), "l"(pl)
                              : "memory");
               } else {
                 atomicAdd(p, x);

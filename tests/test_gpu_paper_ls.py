@@ -3,7 +3,10 @@ SparseStack with zeta = 4, through sk_solve, against the values the paper prints
 (tests/golden/coherent_ls_table.txt). The instance is a fresh draw of the paper's construction, so
 the bars leave room for sampling variation; what they hold is the paper's result: FP32 SparseStack
 within a few percent of the printed residual and kappa(SA), CountSketch's residual and kappa two to
-three orders of magnitude above SparseStack's, and the FP16 rounding rules close to one another."""
+three orders of magnitude above SparseStack's, the FP16 rounding rules close to one another, and, with
+the whole column pre-combined in FP32 before its one binary16 rounding, FP16 closer to FP32 than with
+the default chunking (RN within 15 %, SR and dither within 30 %; the paper's "within 1 %" is not
+reproduced)."""
 import math
 import os
 
@@ -94,5 +97,22 @@ def test_coherent_least_squares_matches_paper_table(sk, dev):
             assert 0.9 * res_ss <= res <= 2.0 * res_ss, (ratio, res, res_ss)
         rs = np.array([r for r, _ in fp16])
         assert rs.max() <= 1.25 * rs.min(), rs
+        # One chunk (R = m: the whole column pre-combined in FP32, one binary16 rounding per output)
+        # removes most of the FP16 excess of the default 8 chunks (measured at d/n = 2: +9 % over FP32
+        # against +28 %), but not all of it: the rounding of S b is comparable to the tail rows' share
+        # of S b in this construction, so the paper's "within 1 %" is not reached (see the design notes).
+        for rule in ("fp16_rn", "fp16_sr", "fp16_dither"):
+            plan = sk.Plan(d, m, 4, rule, seed=31, chunk_rows=m)
+            x = plan.solve(A, b)
+            assert plan.solve_status()[0] == sk.SK_OK
+            res1 = _rel_res(A, b, x)
+            plan.close()
+            res8 = got[{"fp16_rn": "SparseStack-detm", "fp16_sr": "SparseStack-stoch",
+                        "fp16_dither": "SparseStack-dither"}[rule]][0]
+            # RN: +9 % measured at d/n = 2; SR and dither draw their noise from a wider distribution
+            # (+18 % for SR)
+            bar = 1.15 if rule == "fp16_rn" else 1.30
+            assert res_ss <= res1 <= bar * res_ss, (ratio, rule, res1, res_ss)
+            assert res1 <= 1.01 * res8, (ratio, rule, res1, res8)
     del A, b
     torch.cuda.empty_cache()

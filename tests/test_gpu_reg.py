@@ -65,6 +65,7 @@ SHAPES = [
     (12000, 20, 256, 4, 4096, 0),    # d < 1024, B = 64 (long lists); n < 32
     (40000, 64, 4096, 8, 8192, 1),   # list capacity 1: most rows take the overflow path
     (40000, 48, 2048, 8, 2000, 3),   # capacity 3 at B = 256
+    (60000, 64, 1024, 8, 8192, 0),   # B = 128: a group holds 8 blocks, long lists
 ]
 
 
