@@ -83,9 +83,9 @@ typedef enum {
    * Inside a work item the owner kernel adds rows in ascending order, so a chunk processed as one
    * work item has exactly the canonical FP32 chunk total. SK_KERNEL_GLOBAL (chunk totals
    * accumulated in device memory with FP32 reductions, one warp per row; any block height).
-   * SK_KERNEL_REGISTER (chunk accumulation in registers: every 8 lanes own 8 output rows x 32
-   * columns, rows of A are routed to their owners through per-row lists in shared memory, no
-   * floating-point atomics on chip; needs FP32 A, 16-byte aligned with lda a multiple of 4, and
+   * SK_KERNEL_REGISTER (chunk accumulation in registers: every thread owns one output row x 32
+   * columns of a 1024-row group, rows of A are routed to their owners through per-row lists in shared
+   * memory, no floating-point atomics on chip; needs FP32 A, 16-byte aligned with lda a multiple of 4, and
    * atomic mode; SK_ERR_UNSUPPORTED otherwise). AUTO takes the register kernel for FP32 A with
    * k >= 2, n >= 32 and B = d/k <= 512 (except n >= 256 with k = 2) when A's layout allows TMA
    * (and neither SK_PARAM_TILE_COLS nor SK_PARAM_THREADS is set); otherwise the tile kernel, or the global kernel when a block of S is
