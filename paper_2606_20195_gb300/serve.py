@@ -6,7 +6,8 @@ admitted as soon as a slot is free and its device footprint fits the budget. At 
 step the requests admitted in that step are batched: for each rounding rule among them, ONE batched
 sketch launch (sk_batch_launch, a persistent kernel over a device work list) forms S [A_i | b_i] for
 all of them, then each request's FP64 QR and triangular solve run from its sketch
-(sk_solve_sketched), on the same stream. Requests admitted while earlier ones are still on the GPU
+(sk_solve_sketched), on the same stream. Requests whose [A | b] exceeds 256 MiB are not batched: each
+runs on a stream of its own through the single-matrix kernels, which are faster on large matrices. Requests admitted while earlier ones are still on the GPU
 run on other streams and overlap with them. Plans (which own the FP64 QR workspace) are cached per
 (d, k, rule), and batch objects per rule are rebound to the next step's requests once their last
 launch has completed (sk_batch_rebind), so once the pools have warmed up serving allocates no device
@@ -179,6 +180,7 @@ class Server:
         self.batches: dict = {}      # rule -> list of [batch handle, event of its last launch or None]
         self.launches = 0            # batched sketch launches made (one per rule and scheduling step)
         self._rr = 0                 # next stream of the pool
+        self._last_event: dict = {}  # stream index -> event of the last work launched on it
         self.peak_bytes = 0
         self.arena = Arena(self.budget // 4, self.device)
 
@@ -274,18 +276,39 @@ class Server:
         return Ab[:, :req.n].cpu().numpy(), Ab[:, req.n].cpu().numpy()
 
     def _next_stream(self):
-        st = self.streams[self._rr % len(self.streams)]
+        """A stream of the pool with no work outstanding (round robin among those), else the next in
+        turn: work launched in this step should not queue behind a long request on the same stream."""
+        ns = len(self.streams)
+        for i in range(ns):
+            idx = (self._rr + i) % ns
+            ev = self._last_event.get(idx)
+            if ev is None or ev.query():
+                self._rr = idx + 1
+                return self.streams[idx]
+        st = self.streams[self._rr % ns]
         self._rr += 1
         return st
 
+    def _mark(self, st, ev):
+        self._last_event[self.streams.index(st)] = ev
+
+    # Requests whose [A | b] is larger than this are not batched: the single-matrix kernels AUTO picks
+    # (register, global) are faster than the batched kernel on large matrices, and a large item in a
+    # batch would hold back the small requests launched with it.
+    BATCH_MAX_BYTES = 256 << 20
+
     def _launch_group(self, admitted: list):
-        """Jobs for the requests admitted in one scheduling step: per rule, their data, one batched
-        sketch launch over all their [A | b], then each one's QR solve from its sketch."""
+        """Jobs for the requests admitted in one scheduling step: per rule, the small requests' data,
+        one batched sketch launch over all their [A | b], then each one's QR solve from its sketch;
+        every large request on a stream of its own through the single-matrix path."""
         torch = self.torch
         by_rule: dict = {}
-        for req, slot, ranges in admitted:
-            by_rule.setdefault(req.rule, []).append((req, slot, ranges))
         jobs = []
+        for req, slot, ranges in admitted:
+            if req.m * ab_stride(req.n) * 4 > self.BATCH_MAX_BYTES:
+                jobs.append(self._launch_single(req, slot, ranges, self._next_stream()))
+            else:
+                by_rule.setdefault(req.rule, []).append((req, slot, ranges))
         for rule, group in by_rule.items():
             st = self._next_stream()
             with torch.cuda.stream(st):
@@ -307,14 +330,15 @@ class Server:
                     jobs.append({"req": req, "slot": slot, "ranges": ranges, "x": x, "plan": plan, "key": key,
                                  "event": ev, "stream": st, "sketch": it["Y"]})
                 entry[1] = jobs[-1]["event"]  # the batch is free again once its group's last solve is done
+                self._mark(st, entry[1])
         return jobs
 
-    def _launch_single(self, req: Request, slot: int, ranges):
-        """One request on its own (the one-at-a-time baseline and the deterministic mode): the plan's
-        sketch of [A | b] (sk_apply over the n + 1 columns: column n is S b with the rounding bits of
-        column n, as sk_solve forms it), then the FP64 back end (sk_solve_sketched)."""
+    def _launch_single(self, req: Request, slot: int, ranges, st=None):
+        """One request on its own (large requests, the one-at-a-time baseline and the deterministic
+        mode): the plan's sketch of [A | b] (sk_apply over the n + 1 columns: column n is S b with the
+        rounding bits of column n, as sk_solve forms it), then the FP64 back end (sk_solve_sketched)."""
         torch = self.torch
-        st = self.streams[slot % len(self.streams)]
+        st = st if st is not None else self.streams[slot % len(self.streams)]
         Ab, A, b, x, xs, oy = self._views(req, ranges)
         Y = self.arena.buf[oy:]
         with torch.cuda.stream(st):
@@ -324,6 +348,7 @@ class Server:
             skb.sk_solve_sketched(plan.handle, Y, req.n + 1, req.n, x, st)
             ev = torch.cuda.Event()
             ev.record(st)
+        self._mark(st, ev)
         return {"req": req, "slot": slot, "ranges": ranges, "x": x, "plan": plan, "key": key, "event": ev,
                 "stream": st, "sketch": Y}
 

@@ -43,7 +43,8 @@ def _sketch64(sk_host, rule):
     return sk_host.astype(np.float64) if rule == 0 else oracle.halfbits_to_f64(sk_host)
 
 
-def test_batched_results_same_alone_and_in_the_mix(sk, dev):
+@pytest.mark.parametrize("batch_max_bytes", [None, 2 << 20])
+def test_batched_results_same_alone_and_in_the_mix(sk, dev, batch_max_bytes):
     # Atomic mode, batched: the requests of a scheduling step are sketched by one batched launch per
     # rule. Each request's sketch [SA | Sb], in the mix and alone (a batch of one), is within the
     # atomic-mode tolerance of the FP64 sketch of its [A | b] (same S), the two sketches are within
@@ -51,19 +52,26 @@ def test_batched_results_same_alone_and_in_the_mix(sk, dev):
     # reference on the host, to FP32 output precision). The residual ||A x - b|| itself is not
     # compared: with b = A x* + 1e-6 noise the system is nearly consistent and the rounding of S b
     # (FP32 or binary16) already moves it by a few percent from one atomic order to another.
+    # With a 2 MiB batching limit the larger requests take the single-matrix path on streams of their
+    # own while the small ones are batched.
     from paper_2606_20195_gb300 import serve
     reqs = _stream(16, seed=4)
     for r in reqs:
         r.arrival = 0.0  # all at once: the first step batches as many as there are slots
     srv = serve.Server(slots=8, hbm_budget_bytes=2 * 10**9, keep_sketches=True)
+    if batch_max_bytes is not None:
+        srv.BATCH_MAX_BYTES = batch_max_bytes
+    big = [r for r in reqs if r.m * serve.ab_stride(r.n) * 4 > srv.BATCH_MAX_BYTES]
+    assert (len(big) > 0) == (batch_max_bytes is not None)
     stats = srv.run(reqs)
     assert stats["ok"] == len(reqs)
-    assert srv.launches < len(reqs)  # some launch sketched several requests
+    assert srv.launches < len(reqs) - len(big)  # some launch sketched several requests
     alone = _stream(16, seed=4)
     for r in alone:
         s1 = serve.Server(slots=1, hbm_budget_bytes=2 * 10**9, keep_sketches=True)
+        s1.BATCH_MAX_BYTES = srv.BATCH_MAX_BYTES
         s1.run([r])
-        assert r.status == sk.SK_OK and s1.launches == 1
+        assert r.status == sk.SK_OK and s1.launches == (0 if r.rid in {b.rid for b in big} else 1)
         s1.close()
     for rm, ra in zip(reqs, alone):
         A, b = srv.problem(rm)
