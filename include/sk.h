@@ -309,8 +309,10 @@ SK_API sk_status sk_batch_rebind(sk_batch batch, const sk_batch_item* items, int
 /* Override the tile choice: key is SK_PARAM_TILE_COLS, SK_PARAM_THREADS, SK_PARAM_CHUNK_ROWS or
  * SK_PARAM_ITEM_CHUNKS; must be called before the first sk_batch_launch after a create or a rebind. */
 SK_API sk_status sk_batch_set(sk_batch batch, int32_t key, int64_t value);
-/* Zero every Y_i and run the persistent kernel on `stream`: no allocation, no host sync, so the
- * call can be captured into a CUDA graph and replayed. */
+/* Zero every Y_i and run the persistent kernel on `stream`. The first launch after sk_batch_create
+ * or sk_batch_rebind builds the work list and uploads it on `stream` (allocating or growing the
+ * batch's device buffers if needed); later launches allocate nothing and never synchronize, so such
+ * a launch can be captured into a CUDA graph and replayed. */
 SK_API sk_status sk_batch_launch(sk_batch batch, void* stream);
 /* Work-list statistics: number of work items and total bytes of A the batch reads. */
 SK_API sk_status sk_batch_info(sk_batch batch, int64_t* work_items, int64_t* bytes_A);
