@@ -111,8 +111,9 @@ typedef enum {
   /* Rows per group of sk_solve's tree QR (0, the default: as many rows as the GPU's shared memory
    * holds, so a sketch that fits is factored by one launch). Values below 2n are raised to 2n. */
   SK_PARAM_SOLVE_GROUP_ROWS = 11,
-  /* Register kernel: list entries per output row and staged box of rows (0, the default: chosen from
-   * the block height so that a list overflows with probability about 1e-3; 1..64 imposes it). Rows
+  /* Register kernel: list entries per output row and staged box of rows (0, the default: about
+   * lambda + 1.5 sqrt(lambda) for lambda = box rows / B, the mean entries per row and box, e.g. 3 at
+   * B = 512, where about 6 % of the entries overflow; 1..64 imposes it). Rows
    * beyond a full list are added into the chunk totals by FP32 vector reductions instead, with the
    * same result up to FP32 summation order; small values exercise that path. */
   SK_PARAM_LIST_CAP = 12,
