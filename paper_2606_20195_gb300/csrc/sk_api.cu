@@ -1204,14 +1204,26 @@ sk_status sk_solve_status(sk_plan p, double* kappa, void* stream) {
   if (!p) return set_error(SK_ERR_INVALID_ARG, "plan is NULL");
   if (!p->solve_buf) return set_error(SK_ERR_INVALID_ARG, "no sk_solve has run on this plan");
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "sk_solve_status");
+  // One copy of the status word and kappa (adjacent in the scratch layout), ordered on the caller's
+  // stream: a copy on the legacy default stream would also wait for unrelated work queued there.
   unsigned status = 0;
   double kap = 0.0;
-  e = cudaMemcpy(&status, (char*)p->solve_buf + p->solve_status_off, 4, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(e, "reading solve status");
-  e = cudaMemcpy(&kap, (char*)p->solve_buf + p->solve_kappa_off, 8, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(e, "reading kappa");
+  const size_t lo = std::min(p->solve_status_off, p->solve_kappa_off);
+  const size_t hi = std::max(p->solve_status_off + 4, p->solve_kappa_off + 8);
+  unsigned char words[1024];
+  cudaError_t e;
+  if (hi - lo <= sizeof(words)) {
+    e = cudaMemcpyAsync(words, (char*)p->solve_buf + lo, hi - lo, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading solve status");
+    memcpy(&status, words + (p->solve_status_off - lo), 4);
+    memcpy(&kap, words + (p->solve_kappa_off - lo), 8);
+  } else {
+    e = cudaMemcpyAsync(&status, (char*)p->solve_buf + p->solve_status_off, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&kap, (char*)p->solve_buf + p->solve_kappa_off, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading solve status");
+  }
   if (kappa) *kappa = kap;
   if (status & 1u) return set_error(SK_ERR_TIMEOUT, "a grid barrier of the QR kernel timed out");
   if (status & 2u) return set_error(SK_ERR_NUMERIC, "SA is rank deficient (zero pivot in the QR)");

@@ -67,12 +67,26 @@ def device_matrix(m: int, n: int, family: str = "incoherent", seed: int = 0, dev
     raise ValueError(f"unknown family {family!r}")
 
 
+_GENERATORS: dict = {}
+
+
+def device_generator(device, seed: int):
+    """A torch generator of `device` seeded with `seed`: one object per device, re-seeded on every
+    call, so it yields what a fresh generator with that seed would, without creating one per call."""
+    import torch
+    key = str(device)
+    g = _GENERATORS.get(key)
+    if g is None:
+        g = _GENERATORS[key] = torch.Generator(device=device)
+    g.manual_seed(seed)
+    return g
+
+
 def fill_device_matrix(out, family: str = "incoherent", seed: int = 0):
     """device_matrix written into an existing float32 CUDA tensor (same values for the same seed and
     shape): no device allocation, for callers that place matrices in their own memory."""
     import torch
-    g = torch.Generator(device=out.device)
-    g.manual_seed(seed)
+    g = device_generator(out.device, seed)
     m, n = out.shape
     if family == "incoherent":
         torch.randn((m, n), generator=g, out=out)
@@ -82,8 +96,9 @@ def fill_device_matrix(out, family: str = "incoherent", seed: int = 0):
         out.mul_(1e-3)
         q = min(m, n)
         out[:q, :] = 0.0
-        idx = torch.arange(q, device=out.device)
-        out[idx, idx] = 1e3
+        # fill kernels with the value as an argument: an indexed assignment of a Python scalar would
+        # copy it from pageable host memory, which waits for the stream's earlier work
+        out.diagonal().fill_(1e3)
         return out
     raise ValueError(f"unknown family {family!r} for an in-place fill")
 

@@ -170,6 +170,7 @@ class Server:
         self.slots = slots
         self.budget = int(hbm_budget_bytes)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.status_stream = torch.cuda.Stream(device=self.device)  # status reads of finished requests only
         self.free_slots = list(range(slots))
         self.used_bytes = 0
         self.plans: dict = {}        # (d, k, rule) -> list of [Plan, busy, scratch bytes]
@@ -259,8 +260,7 @@ class Server:
         b = A x* + 1e-6 N(0,1)."""
         torch = self.torch
         inputs.fill_device_matrix(A, req.family, seed=req.seed)
-        g = torch.Generator(device=self.device)
-        g.manual_seed(req.seed + 7)
+        g = inputs.device_generator(self.device, req.seed + 7)
         torch.randn(req.n, generator=g, out=xs)
         torch.randn(req.m, generator=g, out=b)
         b.mul_(1e-6).addmv_(A, xs)
@@ -355,7 +355,9 @@ class Server:
     def _finish(self, job, now: float):
         req = job["req"]
         req.done = now
-        status, kappa = job["plan"].solve_status(job["stream"])
+        # The job's event has completed, so its status word is written; read it on a stream of its own
+        # (the job's stream may already hold later requests' work, which a read there would wait for).
+        status, kappa = job["plan"].solve_status(self.status_stream)
         req.status, req.kappa = status, kappa
         if self.keep_results:
             req.x = job["x"].cpu()
