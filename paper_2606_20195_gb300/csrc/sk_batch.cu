@@ -373,8 +373,9 @@ sk_status build_batch(sk_batch_s* b, cudaStream_t st) {
       return set_error(SK_ERR_OOM, "batch status allocation failed");
     }
   }
-  cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), st);
-  cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st);
+  if (cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st) != cudaSuccess)
+    return set_error(SK_ERR_CUDA, "batch status reset: %s", cudaGetErrorString(cudaGetLastError()));
   if (!ensure_dev(&b->d_maps, &b->cap_maps, (size_t)count) || !ensure_dev(&b->d_descs, &b->cap_descs, (size_t)count) ||
       !ensure_dev(&b->d_work, &b->cap_work, work.size()) || !ensure_dev(&b->d_zero, &b->cap_zero, (size_t)count)) {
     free_batch_dev(b);
@@ -383,11 +384,13 @@ sk_status build_batch(sk_batch_s* b, cudaStream_t st) {
   for (int32_t i = 0; i < count; ++i) descs[i].D.tmap = has_map[i] ? (const void*)(b->d_maps + i) : nullptr;
   b->h_descs.swap(descs);
   b->h_work.swap(work);
-  cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * count, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(b->d_descs, b->h_descs.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st);
-  if (!b->h_work.empty())
-    cudaMemcpyAsync(b->d_work, b->h_work.data(), sizeof(BatchWork) * b->h_work.size(), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(b->d_zero, zs.data(), sizeof(ZeroSpan) * count, cudaMemcpyHostToDevice, st);
+  cudaError_t eu = cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * count, cudaMemcpyHostToDevice, st);
+  if (eu == cudaSuccess)
+    eu = cudaMemcpyAsync(b->d_descs, b->h_descs.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st);
+  if (eu == cudaSuccess && !b->h_work.empty())
+    eu = cudaMemcpyAsync(b->d_work, b->h_work.data(), sizeof(BatchWork) * b->h_work.size(), cudaMemcpyHostToDevice, st);
+  if (eu == cudaSuccess) eu = cudaMemcpyAsync(b->d_zero, zs.data(), sizeof(ZeroSpan) * count, cudaMemcpyHostToDevice, st);
+  if (eu != cudaSuccess) return set_error(SK_ERR_CUDA, "batch work-list upload: %s", cudaGetErrorString(eu));
   b->nwork = (int64_t)b->h_work.size();
   b->acc_floats = (int64_t)max_floats;
   b->slot_bytes = slot_max;
