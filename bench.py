@@ -468,9 +468,12 @@ def bench_paper_ls(dev, m=1 << 21, n=1024, ratios=(2, 4, 8, 16, 24), reps=2):
             row = {}
             # the paper's per-element scheme (R = 1, one FP16 atomic per contribution) beside the
             # chunked one, on the coherent problem at the two smallest ratios
-            extra = [("sparsestack_literal", ZETA, "fp16_rn")] if name.startswith("coherent") and r <= 4 else []
+            # and the whole column pre-combined in FP32 before one binary16 rounding (one chunk)
+            extra = ([("sparsestack_literal", ZETA, "fp16_rn"), ("sparsestack_onechunk", ZETA, "fp16_rn")]
+                     if name.startswith("coherent") and r <= 4 else [])
             for meth, k, rname in methods + extra:
-                params = {"kernel": sk.SK_KERNEL_LITERAL, "chunk_rows": 1} if meth.endswith("literal") else {}
+                params = ({"kernel": sk.SK_KERNEL_LITERAL, "chunk_rows": 1} if meth.endswith("literal")
+                          else {"chunk_rows": m} if meth.endswith("onechunk") else {})
                 plan = sk.Plan(d, m, k, sk.RULES[rname], seed=31, **params)
                 x = plan.solve(A, b)
                 torch.cuda.synchronize()
