@@ -23,6 +23,7 @@ def test_arena_first_fit_alignment_and_coalescing():
     for o, n in ((e, 4 * U), (c, U), (d, 4 * U)):
         ar.release(o, n)
     assert ar.free == [(0, 10 * U)]          # everything merged back into one range
+    assert ar.free_floats() == 10 * U
     v = ar.view(ar.alloc(12), (3, 4))
     assert tuple(v.shape) == (3, 4)
 
