@@ -193,3 +193,42 @@ def test_autotune_plan_and_batch(sk, dev, tmp_path, monkeypatch):
         ref = oracle.sketch_f64(it["A"].cpu().numpy(), it["d"], 4, i)
         assert oracle.rel_fro(oracle.halfbits_to_f64(it["Y"].cpu().numpy().view(np.uint16)), ref) <= 2e-3
     sk.sk_batch_destroy(b)
+
+
+@pytest.mark.parametrize("rule", [0, 1, 2, 3])
+def test_batch_item_chunking_independent_of_the_batch(sk, dev, rule):
+    # SK_PARAM_ITEM_CHUNKS: each item's chunk length comes from its own m, so on small-integer data
+    # an item's sketch is the oracle's canonical sketch at that chunk length, bit for bit, alone and
+    # beside other items. k is 1, 4 or 16, so the scale 1/sqrt(k) is a power of two: every chunk
+    # total, its scaled value and every FP32 or binary16 sum of them is exact, whatever the order in
+    # which the batched kernel's atomics add them.
+    import torch
+    shapes = [(50000, 24, 384, 4), (9000, 16, 256, 16), (130000, 8, 128, 1)]
+    def run(which):
+        items = []
+        for i in which:
+            m, n, d, k = shapes[i]
+            A = np.random.default_rng(100 + i).integers(-3, 4, size=(m, n)).astype(np.float32)
+            items.append((i, A, {"A": torch.from_numpy(A).to(dev), "m": m, "n": n, "d": d, "k": k, "seed": 40 + i,
+                                 "Y": torch.empty((d, n), dtype=torch.float32 if rule == 0 else torch.float16,
+                                                  device=dev)}))
+        b = sk.sk_batch_create([it for _, _, it in items], rule)
+        sk.sk_batch_set(b, sk.SK_PARAM_ITEM_CHUNKS, 8)
+        sk.sk_batch_launch(b)
+        torch.cuda.synchronize()
+        out = {}
+        for i, A, it in items:
+            Yn = it["Y"].cpu().numpy()
+            out[i] = (A, Yn if rule == 0 else Yn.view(np.uint16))
+        sk.sk_batch_destroy(b)
+        return out
+    mixed = run([0, 1, 2])
+    for i in range(3):
+        alone = run([i])[i][1]
+        A, got = mixed[i]
+        m, n, d, k = shapes[i]
+        R = max(4096, -(-m // 8))
+        R = -(-R // 256) * 256
+        ref = oracle.sketch_canonical(A, d, k, 40 + i, rule, R)
+        assert np.array_equal(got, ref), (i, np.count_nonzero(got != ref))
+        assert np.array_equal(alone, ref), i
