@@ -195,13 +195,15 @@ def test_autotune_plan_and_batch(sk, dev, tmp_path, monkeypatch):
     sk.sk_batch_destroy(b)
 
 
-@pytest.mark.parametrize("rule", [0, 1, 2, 3])
+@pytest.mark.parametrize("rule", [0, 1, 2])
 def test_batch_item_chunking_independent_of_the_batch(sk, dev, rule):
     # SK_PARAM_ITEM_CHUNKS: each item's chunk length comes from its own m, so on small-integer data
     # an item's sketch is the oracle's canonical sketch at that chunk length, bit for bit, alone and
     # beside other items. k is 1, 4 or 16, so the scale 1/sqrt(k) is a power of two: every chunk
     # total, its scaled value and every FP32 or binary16 sum of them is exact, whatever the order in
-    # which the batched kernel's atomics add them.
+    # which the batched kernel's atomics add them. (Dither is left out: its noise, up to |x| 2^-11,
+    # exceeds half an ulp for mantissas above 1, so it moves exact values off the integer grid and
+    # the binary16 sums of the moved values then depend on the order of the atomics.)
     import torch
     shapes = [(50000, 24, 384, 4), (9000, 16, 256, 16), (130000, 8, 128, 1)]
     def run(which):
