@@ -111,6 +111,20 @@ def make_stream(count: int, rate_hz: float, seed: int = 0, log2_m=(14, 24), ns=(
     return out
 
 
+def partition_step(admitted: list, batch_max_bytes: int):
+    """Split one scheduling step's admitted (request, slot, ranges) entries into those that run alone
+    ([A | b] larger than batch_max_bytes) and, per rounding rule, those sketched by one batched launch;
+    arrival order is kept within each part."""
+    singles, by_rule = [], {}
+    for entry in admitted:
+        req = entry[0]
+        if req.m * ab_stride(req.n) * 4 > batch_max_bytes:
+            singles.append(entry)
+        else:
+            by_rule.setdefault(req.rule, []).append(entry)
+    return singles, by_rule
+
+
 class Arena:
     """First-fit ranges of one float32 device buffer, 256-byte aligned, coalesced on release."""
 
@@ -302,13 +316,8 @@ class Server:
         one batched sketch launch over all their [A | b], then each one's QR solve from its sketch;
         every large request on a stream of its own through the single-matrix path."""
         torch = self.torch
-        by_rule: dict = {}
-        jobs = []
-        for req, slot, ranges in admitted:
-            if req.m * ab_stride(req.n) * 4 > self.BATCH_MAX_BYTES:
-                jobs.append(self._launch_single(req, slot, ranges, self._next_stream()))
-            else:
-                by_rule.setdefault(req.rule, []).append((req, slot, ranges))
+        singles, by_rule = partition_step(admitted, self.BATCH_MAX_BYTES)
+        jobs = [self._launch_single(req, slot, ranges, self._next_stream()) for req, slot, ranges in singles]
         for rule, group in by_rule.items():
             st = self._next_stream()
             with torch.cuda.stream(st):

@@ -42,3 +42,41 @@ def test_x_and_xstar_stay_inside_their_range():
         assert srv._xs_offset(n) + n <= srv.arena._round(nx)  # and ends inside the range
         for o, numel in ranges:
             srv.arena.release(o, numel)
+
+
+def test_partition_step_by_size_and_rule():
+    # One scheduling step: requests whose [A | b] exceeds the limit run alone; the others are grouped
+    # by rounding rule (one batched launch each), in arrival order.
+    def req(rid, m, n, rule):
+        return serve.Request(rid=rid, m=m, n=n, d=16 * n, k=4, rule=rule, family="incoherent", seed=rid)
+    reqs = [req(0, 1 << 20, 64, 1), req(1, 4096, 16, 1), req(2, 8192, 32, 0), req(3, 2048, 16, 1),
+            req(4, 1 << 22, 16, 0), req(5, 4096, 256, 3)]
+    limit = 64 << 20  # bytes of [A | b]
+    admitted = [(r, r.rid, None) for r in reqs]
+    singles, by_rule = serve.partition_step(admitted, limit)
+    assert [e[0].rid for e in singles] == [0, 4]  # 2^20 x 68 and 2^22 x 20 floats exceed 64 MiB
+    assert {rule: [e[0].rid for e in g] for rule, g in by_rule.items()} == {1: [1, 3], 0: [2], 3: [5]}
+    assert serve.ab_stride(16) == 20 and serve.ab_stride(15) == 16 and serve.ab_stride(64) == 68
+    singles, by_rule = serve.partition_step(admitted, 1 << 40)  # nothing too large: all batched
+    assert singles == [] and sum(len(g) for g in by_rule.values()) == len(reqs)
+
+
+def test_next_stream_prefers_idle_streams():
+    # New work goes to a stream whose last work has completed, round robin among those; only when all
+    # are busy does it queue behind one (the next in turn).
+    class Ev:
+        def __init__(self, done):
+            self.done = done
+
+        def query(self):
+            return self.done
+
+    srv = object.__new__(serve.Server)
+    srv.streams = ["s0", "s1", "s2"]
+    srv._rr = 0
+    srv._last_event = {0: Ev(False), 1: Ev(True)}
+    assert srv._next_stream() == "s1"          # s0 busy, s1 idle
+    assert srv._next_stream() == "s2"          # never used: idle
+    srv._mark("s2", Ev(False))
+    srv._last_event[1] = Ev(False)
+    assert srv._next_stream() == "s0"          # all busy: the next in turn (after s2 comes s0)
