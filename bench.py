@@ -631,6 +631,13 @@ def bench_serve(dev, count=1000, warm=200, log2_m=(14, 20), seed=0, rates=(0.5, 
     out["saturated_continuous"] = srv.run(serve.make_stream(count, rate_hz=0.0, seed=seed, log2_m=log2_m))
     out["saturated_continuous"]["batched_launches"] = srv.launches - l0
     srv.close()
+    # the same loop with batching off (every request through the single-matrix path on its own
+    # stream): what overlapping requests alone gives, beside what batching their sketches adds
+    srv = serve.Server(slots=8, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
+    srv.BATCH_MAX_BYTES = 0
+    srv.run(serve.make_stream(warm, rate_hz=0.0, seed=seed + 1, log2_m=log2_m))
+    out["saturated_continuous_no_batching"] = srv.run(serve.make_stream(count, rate_hz=0.0, seed=seed, log2_m=log2_m))
+    srv.close()
     # more slots: larger batches per scheduling step when every request is already waiting
     srv = serve.Server(slots=32, hbm_budget_bytes=120 * 10**9, device=str(dev), keep_results=False)
     srv.run(serve.make_stream(warm, rate_hz=0.0, seed=seed + 1, log2_m=log2_m))

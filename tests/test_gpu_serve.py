@@ -43,7 +43,7 @@ def _sketch64(sk_host, rule):
     return sk_host.astype(np.float64) if rule == 0 else oracle.halfbits_to_f64(sk_host)
 
 
-@pytest.mark.parametrize("batch_max_bytes", [None, 2 << 20])
+@pytest.mark.parametrize("batch_max_bytes", [1 << 40, 2 << 20])
 def test_batched_results_same_alone_and_in_the_mix(sk, dev, batch_max_bytes):
     # Atomic mode, batched: the requests of a scheduling step are sketched by one batched launch per
     # rule. Each request's sketch [SA | Sb], in the mix and alone (a batch of one), is within the
@@ -52,17 +52,16 @@ def test_batched_results_same_alone_and_in_the_mix(sk, dev, batch_max_bytes):
     # reference on the host, to FP32 output precision). The residual ||A x - b|| itself is not
     # compared: with b = A x* + 1e-6 noise the system is nearly consistent and the rounding of S b
     # (FP32 or binary16) already moves it by a few percent from one atomic order to another.
-    # With a 2 MiB batching limit the larger requests take the single-matrix path on streams of their
-    # own while the small ones are batched.
+    # Run with every request batched, and with a 2 MiB limit, under which the larger requests take the
+    # single-matrix path on streams of their own while the small ones are batched.
     from paper_2606_20195_gb300 import serve
     reqs = _stream(16, seed=4)
     for r in reqs:
         r.arrival = 0.0  # all at once: the first step batches as many as there are slots
     srv = serve.Server(slots=8, hbm_budget_bytes=2 * 10**9, keep_sketches=True)
-    if batch_max_bytes is not None:
-        srv.BATCH_MAX_BYTES = batch_max_bytes
+    srv.BATCH_MAX_BYTES = batch_max_bytes
     big = [r for r in reqs if r.m * serve.ab_stride(r.n) * 4 > srv.BATCH_MAX_BYTES]
-    assert (len(big) > 0) == (batch_max_bytes is not None)
+    assert (len(big) > 0) == (batch_max_bytes < (1 << 40))
     stats = srv.run(reqs)
     assert stats["ok"] == len(reqs)
     assert srv.launches < len(reqs) - len(big)  # some launch sketched several requests
